@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the fast damped Gauss-Newton (fLM) step on one GB300.
+
+Workload (one decomposition per GPU; with --gpus N each rank runs its own
+seeded problem, no data exchanged -- replicas, weak scaling):
+  200 x 200 x 200 tensor, rank R = 20, float32 storage; factors with
+  mode-1 collinearity 0.95 and modes 2-3 collinearity 0.81; noise at
+  SNR 40 dB; seeded N(0, 1) initial factors.
+A "step" is one Levenberg-Marquardt trial: Gramians, damped inverses, w,
+core build, core Cholesky + float64 refinement, update, one pass over the
+tensor (MTTKRP and direct residual at the trial point), gain ratio, damping
+update, normalisation, stop test -- captured once in a CUDA graph and
+replayed.  The 32 MB tensor fits in L2, so L2 is flushed (a 256 MB write)
+between timed steps, outside the timed events.
+
+Also reported: the plain float64 form (float64 tensor and float64 core
+Cholesky) on the same problem, time-to-fit of both forms (stop when an
+accepted step changes the relative error by < 1e-9), the MTTKRP pass alone
+against the measured HBM bandwidth, an end-to-end figure through the public
+API with host buffers, and the CPU oracle on the host cores.
+
+--impl reference times the CPU oracle (the float64 numpy implementation in
+oracle/) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fast-dGN iters/s & time-to-fit vs plain FP64 GPU form; p99 served latency"
+DIMS = (200, 200, 200)
+R = 20
+WORKLOAD = "cp3-200^3-R20-collinear(0.95,0.81,0.81)-snr40"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-extras", action="store_true",
+                   help="only the timed steps (no float64 form, time-to-fit, oracle)")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def dist_init(args):
+    import torch
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        n = [i.get("num_threads", 0) for i in info if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(problem, seconds: float):
+    """Oracle LM iterations per second on a bounded sample of the workload."""
+    from oracle import cp_oracle as O
+    t0 = time.perf_counter()
+    res = O.lm_fit(problem.Y, problem.init, mu0=None, max_iter=1, tol=0.0)
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-3)
+    k = max(2, int(seconds / per))
+    t0 = time.perf_counter()
+    res = O.lm_fit(problem.Y, problem.init, mu0=None, max_iter=k, tol=0.0)
+    dt = time.perf_counter() - t0
+    return res.iters / dt, res.iters, dt
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_init(args)
+    # every launch goes to one non-default stream (CUDA graphs cannot capture
+    # the legacy default stream)
+    with torch.cuda.stream(torch.cuda.Stream()):
+        _run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_1205_2584_gb300 import cpdgn as cp
+    from paper_1205_2584_gb300 import synth
+
+    seed = args.seed + rank
+    peaks, peak_src = measured_peaks()
+    prob32 = synth.config2(seed, DIMS, dtype="f32")
+    shape32 = cp.make_shape(DIMS, R, "f32")
+    stream = torch.cuda.current_stream()
+    Y32 = cp.tensor_to_device(prob32.Y, "f32")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def new_state(shape, mode, a0, tol=0.0, max_iter=10 ** 9, mu_max=float("inf")):
+        a = cp.factors_to_device(a0)
+        st = cp.State(shape, a, mu0=-1.0, tau=1e-3, tol=tol, mu_max=mu_max, max_iter=max_iter,
+                      core_mode=mode, refine_iters=4)
+        return st, a
+
+    def timed_steps(st, Y, K, W):
+        nk = st.capture(Y, 1)
+        for _ in range(W):
+            st.launch()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.zero_()                     # L2 flush, outside the timed events
+            ev[i][0].record()
+            st.launch()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        barrier(world)
+        return sum(a.elapsed_time(b) for a, b in ev), nk
+
+    # --- timed region: mixed form on the float32 tensor ---
+    st, a = new_state(shape32, cp.CP_CORE_MIXED, prob32.init)
+    st.init(Y32)
+    with ClockSampler(local) as clk:
+        t_ms, nk = timed_steps(st, Y32, args.steps, args.warmup)
+    status = st.status()
+    t_ms = allmax(t_ms, world)
+    ms_per_step = t_ms / args.steps
+    value = world * args.steps / (t_ms / 1e3)
+
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tensor pass, core factor) + f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R, "tensor_dtype": "f32",
+                      "core": "f32 Cholesky + f64 refinement (4 sweeps)", "l2": "flushed between steps",
+                      "parallelism": f"replicas x{world}", "global_batch": world},
+           "gpu_launches": nk * args.steps, "clocks": clk.summary(),
+           "state_after": {k: status[k] for k in ("iters", "accepted", "rel_err", "mu", "stop_reason",
+                                                  "refine_resid")}}
+
+    if not args.no_extras and rank == 0:
+        # --- MTTKRP pass alone (the tensor-touching kernel) against HBM ---
+        ws = cp.alloc_workspace(shape32)
+        a_in = cp.factors_to_device(prob32.init)
+        m = torch.empty_like(a_in)
+        r2 = torch.empty(1, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            cp._lib.cp_mttkrp_all(cp.ctypes.byref(shape32), cp._ptr(Y32), cp._ptr(a_in), cp._ptr(m),
+                                  cp._ptr(r2), cp._ptr(ws), ws.numel(), cp._stream())
+        evs = []
+        for _ in range(20):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            cp._lib.cp_mttkrp_all(cp.ctypes.byref(shape32), cp._ptr(Y32), cp._ptr(a_in), cp._ptr(m),
+                                  cp._ptr(r2), cp._ptr(ws), ws.numel(), cp._stream())
+            e1.record()
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        mt_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+        bytes_alg = int(np.prod(DIMS)) * 4
+        achieved = bytes_alg / (mt_ms * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": "k_mttkrp<float,float,24> (MTTKRP + residual pass)",
+                           "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                           "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": mt_ms,
+                           "algorithmic_bytes": bytes_alg}
+
+        # --- end to end through the public API with host buffers ---
+        Yh = Y32.cpu().pin_memory()
+        Yd = torch.empty_like(Y32)
+        st_e, _ = new_state(shape32, cp.CP_CORE_MIXED, prob32.init)
+        Yd.copy_(Yh)
+        st_e.init(Yd)
+        for _ in range(args.warmup):
+            st_e.step(Yd)
+        hst = torch.empty(128, dtype=torch.uint8).pin_memory()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            Yd.copy_(Yh, non_blocking=True)
+            st_e.step(Yd)
+            hst.copy_(st_e.status_tensor(), non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1)
+        out["e2e"] = {"value": args.steps / (e2e_ms / 1e3), "unit": "iters/s",
+                      "h2d_bytes_per_step": Yh.numel() * Yh.element_size(), "d2h_bytes_per_step": 128}
+        st_e.close()
+
+        # --- plain float64 form on the float64 tensor ---
+        prob64 = synth.config2(seed, DIMS, dtype="f64")
+        shape64 = cp.make_shape(DIMS, R, "f64")
+        Y64 = cp.tensor_to_device(prob64.Y, "f64")
+        st64, _ = new_state(shape64, cp.CP_CORE_F64, prob64.init)
+        st64.init(Y64)
+        k64 = max(5, args.steps // 5)
+        t64, _ = timed_steps(st64, Y64, k64, 2)
+        out["fp64_form"] = {"value": k64 / (t64 / 1e3), "unit": "iters/s", "ms_per_step": t64 / k64,
+                            "tensor_dtype": "f64", "core": "f64 Cholesky", "steps": k64}
+        out["speedup_vs_fp64_form"] = value / out["fp64_form"]["value"]
+        st64.close()
+
+        # --- time to fit, both forms ---
+        def ttf(shape, Y, prob, mode, cap=3000, chunk=20):
+            s, _ = new_state(shape, mode, prob.init, tol=1e-9, max_iter=cap, mu_max=1e30)
+            s.init(Y)
+            s.capture(Y, chunk)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while True:
+                s.launch()
+                d = s.status()
+                if d["stop"] != 0:
+                    break
+            t = time.perf_counter() - t0
+            s.close()
+            return {"seconds": t, "iters": d["iters"], "accepted": d["accepted"], "rel_err": d["rel_err"],
+                    "stop": d["stop_reason"]}
+        ttf32 = ttf(shape32, Y32, prob32, cp.CP_CORE_MIXED)
+        ttf64 = ttf(shape64, Y64, prob64, cp.CP_CORE_F64)
+        out["time_to_fit"] = {"mixed_f32": ttf32, "plain_f64": ttf64,
+                              "gain": ttf64["seconds"] / ttf32["seconds"]}
+
+        # --- CPU oracle on the host cores (bounded sample) ---
+        rate, iters, secs = oracle_rate(prob32, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": "iters/s", "cores": oracle_threads(),
+                               "kind": "oracle",
+                               "sample": f"first {iters} LM iterations of the same 200^3 R=20 problem "
+                                         f"(float32-rounded tensor in float64), {secs:.1f} s"}
+    st.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import cp_oracle as O
+    from paper_1205_2584_gb300 import synth
+    prob = synth.config2(args.seed, DIMS, dtype="f32")
+    # warm-up iterations, then K timed LM iterations continuing from there
+    w = O.lm_fit(prob.Y, prob.init, mu0=None, max_iter=max(1, args.warmup), tol=0.0)
+    t0 = time.perf_counter()
+    r = O.lm_fit(prob.Y, w.A, mu0=w.mu, max_iter=args.steps, tol=0.0)
+    total = time.perf_counter() - t0
+    times = [0.0] * r.iters
+    value = r.iters / total
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R, "tensor_dtype": "f32-rounded, f64 math"},
+           "cpu_baseline": {"value": value, "unit": "iters/s", "cores": oracle_threads(), "kind": "oracle",
+                            "sample": f"{len(times)} consecutive LM iterations from the seeded start"},
+           "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,223 @@
+/*
+ * cpdgn.h -- C ABI of the GB300 library for the low-complexity damped
+ * Gauss-Newton (Levenberg-Marquardt) step for rank-R CP decomposition of a
+ * dense N-way tensor (Phan, Tichavsky, Cichocki, "Low Complexity Damped
+ * Gauss-Newton Algorithms for CANDECOMP/PARAFAC", arXiv 1205.2584).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Tensor Y (I_1 x ... x I_N) is dense with the first index fastest
+ *    (column-major vec, Sec. 2 and Appendix A).  Its element type is
+ *    cp_shape.y_dtype: float64, float32 or bfloat16.
+ *  - Factors are passed as ONE float64 device buffer `a` holding the paper's
+ *    parameter vector a = [vec A^(1); ...; vec A^(N)] (Eq. vecV): A^(n) is
+ *    I_n x R column-major at offset R * (I_1 + ... + I_{n-1}).  Buffers named
+ *    `m`, `g`, `delta` use the same layout.
+ *  - R x R matrices are column-major; families of them are stored back to
+ *    back (C: N of them; Gamma_nm: N*N of them, (n, m) at index n*N + m).
+ *  - The core system is N R^2 x N R^2, column-major; vectors w and f have
+ *    length N R^2, mode-major, each R x R block column-major (Theorem 1:
+ *    F_n is f[n R^2 : (n+1) R^2] reshaped R x R).
+ *  - Every pointer is a device pointer unless its comment says "host".
+ *    The caller owns every buffer; the library allocates nothing on any
+ *    call below except cp_state_create (a small host-side handle).  All
+ *    device work is enqueued on `stream` and is asynchronous; device
+ *    outputs are valid after the stream is synchronised.
+ *  - Return value: CP_OK or a CP_E* code for errors detected on the host
+ *    (bad arguments, workspace too small, launch failure).  Errors found on
+ *    the device (non-positive pivot, non-finite values) are written to a
+ *    device status word (the `info` argument or cp_status.error); no kernel
+ *    traps.
+ *  - Limits: 2 <= N <= CP_MAX_N, 1 <= R <= CP_MAX_R, every I_n >= 1,
+ *    prod I_n < 2^62.
+ */
+#ifndef CPDGN_H
+#define CPDGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CP_MAX_N 8
+#define CP_MAX_R 32
+
+/* element type of the tensor */
+enum cp_dtype { CP_F64 = 0, CP_F32 = 1, CP_BF16 = 2 };
+
+/* status codes */
+enum cp_code {
+  CP_OK = 0,
+  CP_EINVAL = 1,      /* bad argument: null pointer, N, R or I out of range */
+  CP_ENOTSPD = 2,     /* core system or Gamma^(n) + mu I not positive definite */
+  CP_ENONFINITE = 3,  /* NaN or Inf met on the device */
+  CP_ETIMEOUT = 4,    /* reserved for bounded device waits */
+  CP_ENOMEM = 5,      /* workspace smaller than cp_workspace_bytes() */
+  CP_ECUDA = 6        /* a CUDA runtime call failed */
+};
+
+/* core-system solver of cp_dgn_solve / cp_dgn_step */
+enum cp_core_mode {
+  CP_CORE_F64 = 0,    /* float64 Cholesky of the core system */
+  CP_CORE_MIXED = 1   /* float32 Cholesky + float64 iterative refinement */
+};
+
+/* stop reasons in cp_status.stop */
+enum cp_stop { CP_RUNNING = 0, CP_STOP_TOL = 1, CP_STOP_MU = 2, CP_STOP_MAXIT = 3,
+               CP_STOP_ERROR = 4 };
+
+typedef struct cp_shape {
+  int32_t N;               /* tensor order, 2..CP_MAX_N */
+  int32_t R;               /* rank, 1..CP_MAX_R */
+  int64_t I[CP_MAX_N];     /* I_1..I_N; entries beyond N ignored */
+  int32_t y_dtype;         /* enum cp_dtype of Y; float32 and bfloat16 tensors
+                              are contracted with float32 arithmetic, float64
+                              tensors with float64 arithmetic */
+  int32_t reserved;
+} cp_shape;
+
+typedef struct cp_opts {
+  double mu0;              /* > 0: initial damping; <= 0: tau * max_n max diag Gamma^(n)
+                              (Eq. mu0) */
+  double tau;              /* used when mu0 <= 0 */
+  double tol;              /* stop when an accepted step changes the relative error
+                              epsilon by less than tol (relative) */
+  double mu_max;           /* stop when mu exceeds this (Sec. 4.6: e.g. 1e30) */
+  int32_t max_iter;        /* stop after this many trial steps (accepted or not) */
+  int32_t normalize;       /* 1: spread each component's energy equally over the
+                              modes after every accepted step (Algorithm 1 step 10) */
+  int32_t core_mode;       /* enum cp_core_mode */
+  int32_t refine_iters;    /* max refinement sweeps in CP_CORE_MIXED (e.g. 6) */
+} cp_opts;
+
+/* Device-resident state of one decomposition, 128 bytes. */
+typedef struct cp_status {
+  double mu;               /* current damping */
+  double nu;               /* Nielsen's growth factor */
+  double resid2;           /* ||Y - Y_hat||_F^2 at the current (accepted) factors */
+  double resid2_trial;     /* the same at the last trial factors */
+  double y_norm2;          /* ||Y||_F^2 */
+  double rel_err;          /* epsilon = sqrt(resid2 / y_norm2) */
+  double rho;              /* last gain ratio (Sec. 4.6) */
+  double denom;            /* last Delta a^T (g + mu Delta a) */
+  double refine_resid;     /* last relative residual of the core solve */
+  double reserved_d[3];
+  int32_t iters;           /* trial steps taken */
+  int32_t accepted;        /* accepted steps */
+  int32_t stop;            /* enum cp_stop */
+  int32_t error;           /* enum cp_code of the first device-side error */
+  int32_t last_accepted;   /* 1 if the last trial was accepted */
+  int32_t info;            /* first non-positive pivot (1-based) of the last factorisation */
+  int32_t reserved_i[2];
+} cp_status;
+
+typedef struct cp_state cp_state;   /* opaque host handle */
+
+/* Bytes of device workspace needed by cp_mttkrp_all / cp_fit / cp_dgn_core_build /
+ * cp_dgn_solve (`what` = 0) or by a cp_state (`what` = 1) for this shape and
+ * core mode.  Host-only; no device work.  Returns CP_EINVAL on a bad shape. */
+int cp_workspace_bytes(const cp_shape* shape, int core_mode, int what, size_t* bytes);
+
+/* Gramians (Theorem 1, Eq. Gamma_a; Sec. 3 Eq. ALS):
+ *   C[n]        = A^(n)T A^(n)                       (N R x R matrices)
+ *   Gamma_nm[n*N+m] = Hadamard_{k != n, m} C^(k)     (N*N R x R; all ones when
+ *                                                     no factor remains; the
+ *                                                     diagonal n = m is Gamma^(n))
+ *   Gamma_all   = Hadamard_k C^(k)                   (R x R)
+ * Any output pointer may be NULL to skip it except C. */
+int cp_gram(const cp_shape* shape, const double* a, double* C, double* Gamma_nm,
+            double* Gamma_all, void* stream);
+
+/* All-mode MTTKRP in one pass over Y (Algorithm 1 step 6, Sec. 4.6 Eq. mappingJ):
+ *   m = [vec M_1; ...; vec M_N],  M_n = Y_(n) (A^(N) (.) ... A^(n+1) (.) A^(n-1) (.) ... A^(1)),
+ * and, if resid2 != NULL, *resid2 = ||Y - Y_hat||_F^2 summed directly from the
+ * entries (Sec. 4.6, e_t), in the same pass.  Y is read once.  `ws` must hold
+ * cp_workspace_bytes(shape, 0, 0) bytes.  m and resid2 are overwritten. */
+int cp_mttkrp_all(const cp_shape* shape, const void* Y, const double* a, double* m,
+                  double* resid2, void* ws, size_t ws_bytes, void* stream);
+
+/* Direct residual ||Y - Y_hat||_F^2 -> *resid2 and, if y_norm2 > 0 (host value),
+ * the relative error sqrt(resid2 / y_norm2) -> *rel_err (device scalars;
+ * rel_err may be NULL).  Sec. 6.1 (epsilon). */
+int cp_fit(const cp_shape* shape, const void* Y, const double* a, double y_norm2,
+           double* resid2, double* rel_err, void* ws, size_t ws_bytes, void* stream);
+
+/* Core system of one damped step at factors `a` with MTTKRP `m` and damping
+ * *mu (device scalar), Theorems 1 and 3 in symmetric positive definite form:
+ *   Gt[n]  = (Gamma^(n) + mu I)^{-1}                         (Algorithm 1 step 5)
+ *   w      = [vec(A^(n)T (M_n Gt^(n) - A^(n) Gamma^(n) Gt^(n)))]_n   (Appendix D)
+ *   core   = I + S^T K S,  S = blkdiag(U_n kron L_n),        (lower triangle written)
+ * where K is Theorem 1's kernel (Eq. Knm_a), Gamma^(n) + mu I = L_G L_G^T,
+ * U_n = L_G^{-T} and C^(n) = L_n L_n^T, so that S S^T = Psi_mu (Eq. ZiGZ_LM_a)
+ * and K (I + Psi_mu K)^{-1} = K - K S core^{-1} S^T K.
+ * core: N R^2 x N R^2 float64 column-major (only the lower triangle is
+ * written); Gt: N R x R; w: N R^2.  info (device int, may be NULL) receives
+ * n+1 if Gamma^(n) + mu I or C^(n) is not positive definite. */
+int cp_dgn_core_build(const cp_shape* shape, const double* a, const double* m,
+                      const double* mu, double* core, double* Gt, double* w, int* info,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Solve the core system built by cp_dgn_core_build for f = B_mu w
+ * (Theorem 1, Eq. inverse_f1a):  f = K w - K S core^{-1} S^T K w.
+ * core (in/out): on return holds its lower Cholesky factor (float64).  info
+ * (device int) receives 0, or the 1-based index of the first non-positive
+ * pivot.  a and mu must be those given to cp_dgn_core_build. */
+int cp_dgn_solve(const cp_shape* shape, const double* a, const double* mu, double* core,
+                 const double* w, double* f, int* info, void* ws, size_t ws_bytes,
+                 void* stream);
+
+/* ---- one Levenberg-Marquardt trial on the device (Algorithm 1, Sec. 4.6) ---- */
+
+/* Create a host handle for one decomposition.  a: the caller's float64
+ * factor buffer (R * sum I_n), updated in place by every accepted step;
+ * ws: device workspace of cp_workspace_bytes(shape, opts->core_mode, 1) bytes,
+ * which holds cp_status and every intermediate.  Both must stay valid until
+ * cp_state_destroy.  *out receives the handle (host memory owned by the
+ * library, freed by cp_state_destroy). */
+int cp_state_create(const cp_shape* shape, const cp_opts* opts, double* a, void* ws,
+                    size_t ws_bytes, cp_state** out);
+int cp_state_destroy(cp_state* st);
+
+/* Start a decomposition of Y from the current contents of `a`: one pass over
+ * Y for the MTTKRP, ||Y - Y_hat||^2 and ||Y||^2; sets mu_0 (Eq. mu0 or
+ * opts->mu0), nu = 2 and the counters. */
+int cp_state_init(cp_state* st, const void* Y, void* stream);
+
+/* One damped Gauss-Newton trial: Gramians, damped inverses, w, core build and
+ * solve, update Delta A^(n) = (G_n - A^(n) F_n) Gt^(n) (equivalent to Eq.
+ * fast_low_LM1a), one pass over Y at the trial factors (MTTKRP and direct
+ * residual), gain ratio, accept/reject, Nielsen's mu update, equal-energy
+ * normalisation and the stop test -- all on the device, with no host
+ * synchronisation, so a sequence of calls can be captured in a CUDA graph.
+ * Once the device status says stop != CP_RUNNING every later call is a no-op
+ * on the device. */
+int cp_dgn_step(cp_state* st, const void* Y, void* stream);
+
+/* Capture `steps` consecutive cp_dgn_step calls on `stream` into a CUDA graph
+ * owned by the state (replacing any earlier one).  Nothing runs during the
+ * capture.  The graph reads and writes the same buffers as cp_dgn_step, so
+ * replaying it is exactly `steps` calls of cp_dgn_step on Y.  Host-side
+ * CUDA-graph objects are allocated here and freed by cp_state_destroy. */
+int cp_state_capture(cp_state* st, const void* Y, int steps, void* stream);
+
+/* Launch the captured graph once on `stream` (CP_EINVAL if none). */
+int cp_state_launch(cp_state* st, void* stream);
+
+/* Number of kernel nodes in the captured graph (-1 for a NULL state). */
+int cp_state_graph_kernels(cp_state* st);
+
+/* Device address of the state's cp_status (inside ws). */
+cp_status* cp_state_status(cp_state* st);
+
+/* Device address of an intermediate of the last trial, for inspection:
+ * 0 = m (MTTKRP at the current factors, R*T), 1 = delta (last step, R*T),
+ * 2 = Gt (N R x R), 3 = w (N R^2), 4 = f (N R^2), 5 = a_trial (R*T).
+ * Returns NULL for an unknown id. */
+double* cp_state_buffer(cp_state* st, int id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPDGN_H */

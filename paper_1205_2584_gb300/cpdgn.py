@@ -1,0 +1,281 @@
+"""Thin Python binding of ``libcpdgn.so`` (the C ABI in ``include/cpdgn.h``).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  PyTorch provides device memory and the current CUDA stream.  If
+the library has not been built this module raises at import time; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libcpdgn.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_1205_2584_gb300.build` (nvcc, sm_103a)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+CP_MAX_N = 8
+CP_MAX_R = 32
+CP_F64, CP_F32, CP_BF16 = 0, 1, 2
+CP_CORE_F64, CP_CORE_MIXED = 0, 1
+CODES = {0: "CP_OK", 1: "CP_EINVAL", 2: "CP_ENOTSPD", 3: "CP_ENONFINITE", 4: "CP_ETIMEOUT",
+         5: "CP_ENOMEM", 6: "CP_ECUDA"}
+STOP = {0: "running", 1: "tol", 2: "mu_max", 3: "max_iter", 4: "error"}
+DTYPES = {"f64": CP_F64, "f32": CP_F32, "bf16": CP_BF16}
+TORCH_DTYPE = {CP_F64: torch.float64, CP_F32: torch.float32, CP_BF16: torch.bfloat16}
+
+
+class CPError(RuntimeError):
+    pass
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("R", ctypes.c_int32), ("I", ctypes.c_int64 * CP_MAX_N),
+                ("y_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mu0", ctypes.c_double), ("tau", ctypes.c_double), ("tol", ctypes.c_double),
+                ("mu_max", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("normalize", ctypes.c_int32), ("core_mode", ctypes.c_int32),
+                ("refine_iters", ctypes.c_int32)]
+
+
+class Status(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("nu", ctypes.c_double), ("resid2", ctypes.c_double),
+                ("resid2_trial", ctypes.c_double), ("y_norm2", ctypes.c_double),
+                ("rel_err", ctypes.c_double), ("rho", ctypes.c_double), ("denom", ctypes.c_double),
+                ("refine_resid", ctypes.c_double), ("reserved_d", ctypes.c_double * 3),
+                ("iters", ctypes.c_int32), ("accepted", ctypes.c_int32), ("stop", ctypes.c_int32),
+                ("error", ctypes.c_int32), ("last_accepted", ctypes.c_int32), ("info", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32 * 2)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+assert ctypes.sizeof(Status) == 128
+
+_vp, _sz = ctypes.c_void_p, ctypes.c_size_t
+_sig = {
+    "cp_workspace_bytes": [ctypes.POINTER(Shape), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_sz)],
+    "cp_gram": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp],
+    "cp_mttkrp_all": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _sz, _vp],
+    "cp_fit": [ctypes.POINTER(Shape), _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _sz, _vp],
+    "cp_dgn_core_build": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
+    "cp_dgn_solve": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
+    "cp_state_create": [ctypes.POINTER(Shape), ctypes.POINTER(Opts), _vp, _vp, _sz,
+                        ctypes.POINTER(_vp)],
+    "cp_state_destroy": [_vp],
+    "cp_state_init": [_vp, _vp, _vp],
+    "cp_dgn_step": [_vp, _vp, _vp],
+    "cp_state_capture": [_vp, _vp, ctypes.c_int, _vp],
+    "cp_state_launch": [_vp, _vp],
+    "cp_state_graph_kernels": [_vp],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.cp_state_status.argtypes = [_vp]
+_lib.cp_state_status.restype = _vp
+_lib.cp_state_buffer.argtypes = [_vp, ctypes.c_int]
+_lib.cp_state_buffer.restype = _vp
+
+EXPORTED = list(_sig) + ["cp_state_status", "cp_state_buffer"]
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise CPError(f"{what} failed: {CODES.get(rc, rc)}")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_shape(dims: Sequence[int], R: int, y_dtype) -> Shape:
+    s = Shape()
+    s.N = len(dims)
+    s.R = int(R)
+    for n, I in enumerate(dims):
+        s.I[n] = int(I)
+    s.y_dtype = DTYPES[y_dtype] if isinstance(y_dtype, str) else int(y_dtype)
+    return s
+
+
+def workspace_bytes(shape: Shape, core_mode: int = CP_CORE_F64, state: bool = False) -> int:
+    out = _sz(0)
+    _check(_lib.cp_workspace_bytes(ctypes.byref(shape), core_mode, 1 if state else 0,
+                                   ctypes.byref(out)), "cp_workspace_bytes")
+    return out.value
+
+
+def alloc_workspace(shape: Shape, core_mode: int = CP_CORE_F64, state: bool = False,
+                    device="cuda") -> torch.Tensor:
+    nb = workspace_bytes(shape, core_mode, state)
+    return torch.empty(max(nb, 256), dtype=torch.uint8, device=device)
+
+
+def factors_to_device(factors, device="cuda") -> torch.Tensor:
+    """Stack I_n x R float64 factors into the parameter vector a (column-major blocks)."""
+    parts = [torch.as_tensor(f, dtype=torch.float64).t().contiguous().reshape(-1) for f in factors]
+    return torch.cat(parts).to(device)
+
+
+def split_factors(a: torch.Tensor, dims: Sequence[int], R: int):
+    out, off = [], 0
+    for I in dims:
+        out.append(a[off:off + I * R].reshape(R, I).t())
+        off += I * R
+    return out
+
+
+def tensor_to_device(Y, y_dtype: str, device="cuda") -> torch.Tensor:
+    """Column-major (first index fastest) device copy of a numpy tensor."""
+    import numpy as np
+    flat = np.asarray(Y, dtype=np.float64).ravel(order="F")
+    return torch.from_numpy(flat).to(TORCH_DTYPE[DTYPES[y_dtype]]).to(device)
+
+
+# ---------------------------------------------------------------------------
+# stand-alone calls
+# ---------------------------------------------------------------------------
+
+def gram(shape: Shape, a: torch.Tensor, stream=None):
+    N, R = shape.N, shape.R
+    C = torch.empty(N * R * R, dtype=torch.float64, device=a.device)
+    Gnm = torch.empty(N * N * R * R, dtype=torch.float64, device=a.device)
+    Gall = torch.empty(R * R, dtype=torch.float64, device=a.device)
+    _check(_lib.cp_gram(ctypes.byref(shape), _ptr(a), _ptr(C), _ptr(Gnm), _ptr(Gall), _stream(stream)),
+           "cp_gram")
+    return C, Gnm, Gall
+
+
+def mttkrp_all(shape: Shape, Y: torch.Tensor, a: torch.Tensor, want_resid=True, ws=None, stream=None):
+    m = torch.empty_like(a)
+    r2 = torch.empty(1, dtype=torch.float64, device=a.device) if want_resid else None
+    ws = ws if ws is not None else alloc_workspace(shape)
+    _check(_lib.cp_mttkrp_all(ctypes.byref(shape), _ptr(Y), _ptr(a), _ptr(m), _ptr(r2), _ptr(ws),
+                              ws.numel(), _stream(stream)), "cp_mttkrp_all")
+    return m, r2
+
+
+def fit(shape: Shape, Y: torch.Tensor, a: torch.Tensor, y_norm2: float = 0.0, ws=None, stream=None):
+    r2 = torch.empty(1, dtype=torch.float64, device=a.device)
+    rel = torch.empty(1, dtype=torch.float64, device=a.device)
+    ws = ws if ws is not None else alloc_workspace(shape)
+    _check(_lib.cp_fit(ctypes.byref(shape), _ptr(Y), _ptr(a), ctypes.c_double(y_norm2), _ptr(r2),
+                       _ptr(rel), _ptr(ws), ws.numel(), _stream(stream)), "cp_fit")
+    return r2, rel
+
+
+def core_build(shape: Shape, a: torch.Tensor, m: torch.Tensor, mu: torch.Tensor, ws=None, stream=None):
+    N, R = shape.N, shape.R
+    n = N * R * R
+    core = torch.zeros(n * n, dtype=torch.float64, device=a.device)
+    Gt = torch.empty(N * R * R, dtype=torch.float64, device=a.device)
+    w = torch.empty(n, dtype=torch.float64, device=a.device)
+    info = torch.zeros(1, dtype=torch.int32, device=a.device)
+    ws = ws if ws is not None else alloc_workspace(shape)
+    _check(_lib.cp_dgn_core_build(ctypes.byref(shape), _ptr(a), _ptr(m), _ptr(mu), _ptr(core), _ptr(Gt),
+                                  _ptr(w), _ptr(info), _ptr(ws), ws.numel(), _stream(stream)),
+           "cp_dgn_core_build")
+    return core, Gt, w, info
+
+
+def core_solve(shape: Shape, a: torch.Tensor, mu: torch.Tensor, core: torch.Tensor, w: torch.Tensor,
+               ws=None, stream=None):
+    f = torch.empty_like(w)
+    info = torch.zeros(1, dtype=torch.int32, device=a.device)
+    ws = ws if ws is not None else alloc_workspace(shape)
+    _check(_lib.cp_dgn_solve(ctypes.byref(shape), _ptr(a), _ptr(mu), _ptr(core), _ptr(w), _ptr(f),
+                             _ptr(info), _ptr(ws), ws.numel(), _stream(stream)), "cp_dgn_solve")
+    return f, info
+
+
+# ---------------------------------------------------------------------------
+# device-resident LM state
+# ---------------------------------------------------------------------------
+
+class State:
+    """One decomposition whose factors, damping and counters live on the GPU."""
+
+    BUF_M, BUF_DELTA, BUF_GT, BUF_W, BUF_F, BUF_AT = range(6)
+
+    def __init__(self, shape: Shape, a: torch.Tensor, *, mu0: float = -1.0, tau: float = 1e-3,
+                 tol: float = 0.0, mu_max: float = 1e30, max_iter: int = 1000, normalize: bool = True,
+                 core_mode: int = CP_CORE_F64, refine_iters: int = 4):
+        assert a.dtype == torch.float64 and a.is_cuda and a.is_contiguous()
+        self.shape = shape
+        self.a = a
+        self.opts = Opts(mu0=mu0, tau=tau, tol=tol, mu_max=mu_max, max_iter=max_iter,
+                         normalize=1 if normalize else 0, core_mode=core_mode, refine_iters=refine_iters)
+        self.ws = alloc_workspace(shape, core_mode, state=True, device=a.device)
+        h = ctypes.c_void_p()
+        _check(_lib.cp_state_create(ctypes.byref(shape), ctypes.byref(self.opts), _ptr(a), _ptr(self.ws),
+                                    self.ws.numel(), ctypes.byref(h)), "cp_state_create")
+        self._h = h
+        self._status_ptr = _lib.cp_state_status(h)
+        self._host_status = torch.empty(128, dtype=torch.uint8).pin_memory()
+
+    def init(self, Y: torch.Tensor, stream=None):
+        _check(_lib.cp_state_init(self._h, _ptr(Y), _stream(stream)), "cp_state_init")
+
+    def step(self, Y: torch.Tensor, stream=None):
+        _check(_lib.cp_dgn_step(self._h, _ptr(Y), _stream(stream)), "cp_dgn_step")
+
+    def capture(self, Y: torch.Tensor, steps: int, stream=None):
+        """Capture `steps` steps into the state's CUDA graph (nothing runs)."""
+        _check(_lib.cp_state_capture(self._h, _ptr(Y), int(steps), _stream(stream)), "cp_state_capture")
+        return _lib.cp_state_graph_kernels(self._h)
+
+    def launch(self, stream=None):
+        _check(_lib.cp_state_launch(self._h, _stream(stream)), "cp_state_launch")
+
+    @property
+    def graph_kernels(self) -> int:
+        return _lib.cp_state_graph_kernels(self._h)
+
+    def status_tensor(self) -> torch.Tensor:
+        """Device view (128 bytes) of the state's cp_status."""
+        off = self._status_ptr - self.ws.data_ptr()
+        return self.ws[off:off + 128]
+
+    def status(self, stream=None) -> dict:
+        """Synchronous read of the device status (copies 128 bytes)."""
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self._host_status.copy_(self.status_tensor(), non_blocking=True)
+        st.synchronize()
+        s = Status.from_buffer_copy(bytes(self._host_status.numpy()))
+        d = s.as_dict()
+        d["stop_reason"] = STOP.get(d["stop"], d["stop"])
+        return d
+
+    def buffer(self, which: int, count: int) -> torch.Tensor:
+        p = _lib.cp_state_buffer(self._h, which)
+        off = p - self.ws.data_ptr()
+        return self.ws[off:off + 8 * count].view(torch.float64)
+
+    def close(self):
+        if self._h:
+            _lib.cp_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,596 @@
+// One damped Gauss-Newton / Levenberg-Marquardt trial on the device
+// (Algorithm 1 with the damping control of Sec. 4.6), and the stand-alone
+// core-system calls of the C ABI.
+//
+// Kernel sequence of cp_dgn_step (no host synchronisation; graph-capturable):
+//   k_step_begin      clear per-trial flags, zero the trial MTTKRP
+//   k_gram_cp/_had    C^(n), P^(n) = A^(n)T M_n, Gamma^(n,m), Gamma
+//   k_mode_prep       Gt^(n), U_n, L_n, w                 (Algorithm 1 steps 5-7)
+//   k_core_w/_fill    core = I + S^T K S                   (step 8-9, SPD form)
+//   chol_factor       core = L L^T (float64, or float32 in the mixed mode)
+//   solve             f = K w - K S core^{-1} S^T K w      (step 9)
+//   k_update          Delta A^(n) = (G_n - A^(n) F_n) Gt^(n), trial factors,
+//                     Delta^T (g + mu Delta) and column norms (steps 10-11)
+//   mttkrp            M_n and ||E||^2 at the trial factors (one pass over Y)
+//   k_control         gain ratio, accept iff the error decreased, Nielsen's
+//                     mu update, equal-energy scales, stop test (Sec. 4.6)
+//   k_commit          on acceptance: A <- scaled trial factors, M <- rescaled
+//                     trial MTTKRP (normalisation does not need a new pass:
+//                     column r of M_n scales by 1/s_r^(n) when prod_n s_r^(n) = 1)
+#include <new>
+
+#include "common.cuh"
+
+namespace cpdgn {
+
+int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, double* resid2,
+                  const int* skip, cudaStream_t s);
+int launch_gram(const Dims& d, const double* a, const double* m, double* C, double* P,
+                double* Gnm, double* Gall, const int* skip, cudaStream_t s);
+int launch_mode_prep(const Dims& d, const double* C, const double* Gnm, const double* P,
+                     const double* mu, double* Gt, double* U, double* LC, double* w, int* info,
+                     const int* skip, cudaStream_t s);
+int launch_core_w(const Dims& d, const double* Gnm, const double* LC, const double* U, double* Wp,
+                  const int* skip, cudaStream_t s);
+template <typename T>
+int launch_core_fill(const Dims& d, const double* LC, const double* U, const double* Wp, T* core,
+                     const int* skip, cudaStream_t s);
+int launch_apply_K(const Dims& d, const double* Gnm, const double* x, const double* base, double* out,
+                   const int* skip, cudaStream_t s);
+int launch_apply_S(const Dims& d, const double* LC, const double* U, const double* x, double* out,
+                   const int* skip, cudaStream_t s);
+int launch_apply_ST(const Dims& d, const double* LC, const double* U, const double* Gnm,
+                    const double* x, int kx, const double* b, const double* y, double* out,
+                    const int* skip, cudaStream_t s);
+template <typename T>
+int chol_factor(T* A, int64_t n, int* info, const int* skip, cudaStream_t s);
+template <typename T, typename TX>
+int chol_solve(const T* L, int64_t n, TX* x, TX* tmp, TX* y, const int* skip, cudaStream_t s);
+
+// scalar slots (doubles) inside S_SCAL
+enum { SC_R2T = 0, SC_YN2 = 1, SC_R2 = 2, SC_REFN = 3, SC_BN = 4 };
+// int slots inside S_INFO
+enum { IN_INFO = 0, IN_COMMIT = 1, IN_ZERO = 2 };
+
+struct Bufs {
+  double *C, *Gnm, *Gall, *P, *LC, *U, *Gt, *w, *Kw, *b, *y, *Z, *res, *dcor, *f, *Wp;
+  float *core32, *vec32;
+  double *part, *scal;
+  int* info;
+  cp_status* status;
+  double *m, *mt, *at, *delta, *scale, *mu;
+  double* core64;
+};
+
+static Bufs carve(const Layout& L, void* ws) {
+  char* base = static_cast<char*>(ws);
+  Bufs b;
+  b.C = reinterpret_cast<double*>(base + L.off[S_C]);
+  b.Gnm = reinterpret_cast<double*>(base + L.off[S_GNM]);
+  b.Gall = reinterpret_cast<double*>(base + L.off[S_GALL]);
+  b.P = reinterpret_cast<double*>(base + L.off[S_P]);
+  b.LC = reinterpret_cast<double*>(base + L.off[S_LC]);
+  b.U = reinterpret_cast<double*>(base + L.off[S_U]);
+  b.Gt = reinterpret_cast<double*>(base + L.off[S_GT]);
+  b.w = reinterpret_cast<double*>(base + L.off[S_W]);
+  b.Kw = reinterpret_cast<double*>(base + L.off[S_KW]);
+  b.b = reinterpret_cast<double*>(base + L.off[S_B]);
+  b.y = reinterpret_cast<double*>(base + L.off[S_Y]);
+  b.Z = reinterpret_cast<double*>(base + L.off[S_Z]);
+  b.res = reinterpret_cast<double*>(base + L.off[S_RES]);
+  b.dcor = reinterpret_cast<double*>(base + L.off[S_D]);
+  b.f = reinterpret_cast<double*>(base + L.off[S_F]);
+  b.Wp = reinterpret_cast<double*>(base + L.off[S_WP]);
+  b.core32 = reinterpret_cast<float*>(base + L.off[S_CORE32]);
+  b.vec32 = reinterpret_cast<float*>(base + L.off[S_VEC32]);
+  b.part = reinterpret_cast<double*>(base + L.off[S_PART]);
+  b.scal = reinterpret_cast<double*>(base + L.off[S_SCAL]);
+  b.info = reinterpret_cast<int*>(base + L.off[S_INFO]);
+  b.status = reinterpret_cast<cp_status*>(base + L.off[S_STATUS]);
+  b.m = reinterpret_cast<double*>(base + L.off[S_M]);
+  b.mt = reinterpret_cast<double*>(base + L.off[S_MT]);
+  b.at = reinterpret_cast<double*>(base + L.off[S_AT]);
+  b.delta = reinterpret_cast<double*>(base + L.off[S_DELTA]);
+  b.scale = reinterpret_cast<double*>(base + L.off[S_SCALE]);
+  b.mu = reinterpret_cast<double*>(base + L.off[S_MU]);
+  b.core64 = reinterpret_cast<double*>(base + L.off[S_CORE64]);
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+// vec32 <- float(src)   or   dst (+)= double(vec32)
+__global__ void k_cvt(int64_t n, const double* src, float* x32, const float* y32, double* dst,
+                      int accumulate, const int* skip) {
+  if (skip && *skip) return;
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (src) x32[i] = float(src[i]);
+  if (dst) dst[i] = accumulate ? dst[i] + double(y32[i]) : double(y32[i]);
+}
+
+// relative residual ||res|| / ||b|| of the last refinement sweep -> scal[SC_REFN]
+__global__ void k_refine_norm(int64_t n, const double* res, const double* b, double* scal,
+                              const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double sh[256];
+  double sr = 0, sb = 0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) {
+    sr = fma(res[i], res[i], sr);
+    sb = fma(b[i], b[i], sb);
+  }
+  const double tr = block_sum<256>(sr, sh);
+  const double tb = block_sum<256>(sb, sh);
+  if (threadIdx.x == 0) scal[SC_REFN] = (tb > 0) ? sqrt(tr / tb) : 0.0;
+}
+
+__global__ void k_step_begin(int64_t nm, double* mt, double* scal, int* info) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    info[IN_INFO] = 0;
+    info[IN_COMMIT] = 0;
+    scal[SC_R2T] = 0.0;
+  }
+  for (; i < nm; i += int64_t(gridDim.x) * blockDim.x) mt[i] = 0.0;
+}
+
+// Delta A and trial factors; CTA = (mode n, block of kUpdRows rows); thread = (row, r).
+__global__ void __launch_bounds__(kUpdRows * 32) k_update(Dims d, const double* a, const double* m,
+                                                          const double* Gnm, const double* Gt,
+                                                          const double* f, const double* mu,
+                                                          double* delta, double* at, double* part,
+                                                          const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double Gam[CP_MAX_R * CP_MAX_R], Fn[CP_MAX_R * CP_MAX_R], Gtn[CP_MAX_R * CP_MAX_R];
+  __shared__ double Arow[kUpdRows][CP_MAX_R], H[kUpdRows][CP_MAX_R], Q[kUpdRows][CP_MAX_R];
+  __shared__ double red[kUpdRows * 32];
+  const int R = d.R, RR = d.RR, N = d.N;
+  int b = blockIdx.x, n = 0;
+  for (; n < N; ++n) {
+    const int nb = int((d.I[n] + kUpdRows - 1) / kUpdRows);
+    if (b < nb) break;
+    b -= nb;
+  }
+  const int64_t In = d.I[n];
+  const int64_t i0 = int64_t(b) * kUpdRows;
+  const int tid = threadIdx.x;
+  const int row = tid / 32, r = tid % 32;
+  const int64_t i = i0 + row;
+  const bool act = (r < R) && (i < In);
+  for (int e = tid; e < RR; e += blockDim.x) {
+    Gam[e] = Gnm[(int64_t(n) * N + n) * RR + e];
+    Fn[e] = f[int64_t(n) * RR + e];
+    Gtn[e] = Gt[int64_t(n) * RR + e];
+  }
+  const double* An = a + d.aoff[n];
+  const double* Mn = m + d.aoff[n];
+  Arow[row][r] = act ? An[i + In * r] : 0.0;
+  __syncthreads();
+  double g = 0.0;
+  if (act) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int s = 0; s < R; ++s) {
+      s1 = fma(Arow[row][s], Gam[s + R * r], s1);
+      s2 = fma(Arow[row][s], Fn[s + R * r], s2);
+    }
+    g = Mn[i + In * r] - s1;          // gradient block G_n = M_n - A^(n) Gamma^(n)
+    H[row][r] = g - s2;               // G_n - A^(n) F_n
+  }
+  __syncthreads();
+  double dl = 0.0, contrib = 0.0, at2 = 0.0;
+  if (act) {
+    double s = 0.0;
+    for (int c = 0; c < R; ++c) s = fma(H[row][c], Gtn[c + R * r], s);
+    dl = s;
+    const double muv = *mu;
+    contrib = dl * (g + muv * dl);
+    const double av = Arow[row][r] + dl;
+    at2 = av * av;
+    delta[d.aoff[n] + i + In * r] = dl;
+    at[d.aoff[n] + i + In * r] = av;
+  }
+  Q[row][r] = at2;
+  const double den = block_sum<kUpdRows * 32>(contrib, red);
+  double* pc = part + int64_t(blockIdx.x) * (1 + R);
+  if (tid == 0) pc[0] = den;
+  if (tid < R) {
+    double s = 0.0;
+    for (int q = 0; q < kUpdRows; ++q) s += Q[q][tid];
+    pc[1 + tid] = s;
+  }
+}
+
+__global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_status* st,
+                          double* scal, int* info, double* scale) {
+  __shared__ double sh[256];
+  __shared__ double norms[CP_MAX_N * CP_MAX_R];
+  __shared__ int s_acc;
+  if (st->stop != CP_RUNNING) return;
+  const int tid = threadIdx.x;
+  const int R = d.R, N = d.N;
+  double v = 0.0;
+  for (int64_t c = tid; c < nparts; c += 256) v += part[c * (1 + R)];
+  const double den = block_sum<256>(v, sh);
+  // column norms of the trial factors, per mode, summed in CTA order
+  if (tid < N * R) {
+    const int n = tid / R, r = tid % R;
+    int64_t c0 = 0;
+    for (int k = 0; k < n; ++k) c0 += (d.I[k] + kUpdRows - 1) / kUpdRows;
+    const int64_t c1 = c0 + (d.I[n] + kUpdRows - 1) / kUpdRows;
+    double s = 0.0;
+    for (int64_t c = c0; c < c1; ++c) s += part[c * (1 + R) + 1 + r];
+    norms[tid] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double r2 = st->resid2;
+    const double r2t = scal[SC_R2T];
+    const int bad = info[IN_INFO];
+    const bool accept = (bad == 0) && isfinite(r2t) && (r2t < r2);
+    const double rho = (den > 0.0 && isfinite(r2t)) ? (r2 - r2t) / den : 0.0;
+    double mu = st->mu, nu = st->nu;
+    if (rho > 0.0) {
+      const double t = 2.0 * rho - 1.0;
+      const double fac = 1.0 - t * t * t;
+      mu *= (fac > 1.0 / 3.0) ? fac : 1.0 / 3.0;
+      nu = 2.0;
+    } else {
+      mu *= nu;
+      nu *= 2.0;
+    }
+    st->iters += 1;
+    st->rho = rho;
+    st->denom = den;
+    st->resid2_trial = r2t;
+    st->info = bad;
+    st->refine_resid = scal[SC_REFN];
+    st->mu = mu;
+    st->nu = nu;
+    st->last_accepted = accept ? 1 : 0;
+    if (accept) {
+      const double e_old = sqrt(r2 / st->y_norm2), e_new = sqrt(r2t / st->y_norm2);
+      st->accepted += 1;
+      st->resid2 = r2t;
+      st->rel_err = e_new;
+      if (e_old > 0.0 && fabs(e_old - e_new) / e_old < o.tol) st->stop = CP_STOP_TOL;
+    }
+    if (st->stop == CP_RUNNING && mu > o.mu_max) st->stop = CP_STOP_MU;
+    if (st->stop == CP_RUNNING && st->iters >= o.max_iter) st->stop = CP_STOP_MAXIT;
+    info[IN_COMMIT] = accept ? 1 : 0;
+    s_acc = accept ? 1 : 0;
+  }
+  __syncthreads();
+  // equal-energy scales: s_r^(n) = lambda_r^(1/N) / ||a_r^(n)||, lambda_r = prod_n ||a_r^(n)||
+  if (tid < R) {
+    const int r = tid;
+    bool ok = (o.normalize != 0) && s_acc;
+    double lam = 1.0;
+    for (int n = 0; n < N; ++n) {
+      const double nr = sqrt(norms[n * R + r]);
+      if (!(nr > 0.0)) ok = false;
+      lam *= nr;
+    }
+    const double tgt = ok ? pow(lam, 1.0 / N) : 1.0;
+    for (int n = 0; n < N; ++n) scale[n * R + r] = ok ? tgt / sqrt(norms[n * R + r]) : 1.0;
+  }
+}
+
+__global__ void k_commit(Dims d, const int* commit, const double* at, const double* mt,
+                         const double* scale, double* a, double* m) {
+  if (!*commit) return;
+  const int64_t tot = d.T * d.R;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < tot;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    int n = 0;
+    while (n + 1 < d.N && idx >= d.aoff[n + 1]) ++n;
+    const int r = int((idx - d.aoff[n]) / d.I[n]);
+    const double s = scale[n * d.R + r];
+    a[idx] = at[idx] * s;
+    m[idx] = mt[idx] / s;
+  }
+}
+
+__global__ void k_sumsq(const void* Y, int dtype, int64_t J, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < J; i += int64_t(gridDim.x) * 256) {
+    double v;
+    if (dtype == CP_F64) v = static_cast<const double*>(Y)[i];
+    else if (dtype == CP_F32) v = static_cast<const float*>(Y)[i];
+    else v = __bfloat162float(static_cast<const __nv_bfloat16*>(Y)[i]);
+    s = fma(v, v, s);
+  }
+  const double t = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) atomicAdd(out, t);
+}
+
+__global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double* scal, cp_status* st,
+                              double* mu_copy) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double mx = 0.0;
+  for (int n = 0; n < d.N; ++n)
+    for (int r = 0; r < d.R; ++r) {
+      const double v = Gnm[(int64_t(n) * d.N + n) * d.RR + r + d.R * r];
+      mx = v > mx ? v : mx;
+    }
+  cp_status s;
+  s.mu = (o.mu0 > 0.0) ? o.mu0 : o.tau * mx;
+  s.nu = 2.0;
+  s.resid2 = scal[SC_R2];
+  s.resid2_trial = scal[SC_R2];
+  s.y_norm2 = scal[SC_YN2];
+  s.rel_err = sqrt(scal[SC_R2] / scal[SC_YN2]);
+  s.rho = 0.0;
+  s.denom = 0.0;
+  s.refine_resid = 0.0;
+  s.reserved_d[0] = s.reserved_d[1] = s.reserved_d[2] = 0.0;
+  s.iters = 0;
+  s.accepted = 0;
+  s.stop = CP_RUNNING;
+  s.error = 0;
+  s.last_accepted = 0;
+  s.info = 0;
+  s.reserved_i[0] = s.reserved_i[1] = 0;
+  *st = s;
+  *mu_copy = s.mu;
+}
+
+// ---------------------------------------------------------------------------
+// shared pieces of the core solve
+// ---------------------------------------------------------------------------
+
+// f = K w - K S y with y = core^{-1} S^T K w, given factorised core.
+// mode CP_CORE_F64: L64 holds the float64 factor; CP_CORE_MIXED: L32 holds the
+// float32 factor and the solution is refined with the float64 operator.
+static int solve_core(const Dims& d, const Bufs& B, const double* L64, const float* L32, int mode,
+                      int refine_iters, const int* skip, cudaStream_t s) {
+  const int64_t n = d.ncore;
+  CP_TRY(launch_apply_K(d, B.Gnm, B.w, nullptr, B.Kw, skip, s));                  // Kw
+  CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Kw, 0, nullptr, nullptr, B.b, skip, s));  // b = S^T K w
+  const unsigned g = unsigned((n + 255) / 256);
+  if (mode == CP_CORE_F64) {
+    CP_CUDA(cudaMemcpyAsync(B.res, B.b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CP_TRY((chol_solve<double, double>(L64, n, B.res, B.dcor, B.y, skip, s)));
+  } else {
+    float* x32 = B.vec32;
+    float* t32 = B.vec32 + n;
+    // y = core32^{-1} b, then y += core32^{-1} (b - y - S^T K S y), refine_iters times
+    k_cvt<<<g, 256, 0, s>>>(n, B.b, x32, nullptr, nullptr, 0, skip);
+    CP_TRY((chol_solve<float, float>(L32, n, x32, t32, x32, skip, s)));
+    k_cvt<<<g, 256, 0, s>>>(n, nullptr, nullptr, x32, B.y, 0, skip);
+    for (int it = 0; it < refine_iters; ++it) {
+      CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, skip, s));
+      CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Z, 1, B.b, B.y, B.res, skip, s));
+      k_cvt<<<g, 256, 0, s>>>(n, B.res, x32, nullptr, nullptr, 0, skip);
+      CP_TRY((chol_solve<float, float>(L32, n, x32, t32, x32, skip, s)));
+      k_cvt<<<g, 256, 0, s>>>(n, nullptr, nullptr, x32, B.y, 1, skip);
+    }
+    CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, skip, s));
+    CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Z, 1, B.b, B.y, B.res, skip, s));
+    k_refine_norm<<<1, 256, 0, s>>>(n, B.res, B.b, B.scal, skip);
+  }
+  CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, skip, s));                        // Z = S y
+  CP_TRY(launch_apply_K(d, B.Gnm, B.Z, B.Kw, B.f, skip, s));                      // f = Kw - K Z
+  return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
+}
+
+}  // namespace cpdgn
+
+using namespace cpdgn;
+
+struct cp_state {
+  Dims d;
+  cp_opts o;
+  double* a;
+  void* ws;
+  Layout L;
+  Bufs B;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_steps = 0;
+  int graph_kernels = 0;
+};
+
+static void drop_graph(cp_state* st) {
+  if (st->exec) cudaGraphExecDestroy(st->exec);
+  if (st->graph) cudaGraphDestroy(st->graph);
+  st->exec = nullptr;
+  st->graph = nullptr;
+  st->graph_steps = 0;
+  st->graph_kernels = 0;
+}
+
+extern "C" int cp_workspace_bytes(const cp_shape* shape, int core_mode, int what, size_t* bytes) {
+  Dims d;
+  CP_TRY(make_dims(shape, &d));
+  if (!bytes || (core_mode != CP_CORE_F64 && core_mode != CP_CORE_MIXED)) return CP_EINVAL;
+  Layout L;
+  make_layout(d, core_mode, what ? 1 : 0, &L);
+  *bytes = L.total;
+  return CP_OK;
+}
+
+extern "C" int cp_dgn_core_build(const cp_shape* shape, const double* a, const double* m,
+                                 const double* mu, double* core, double* Gt, double* w, int* info,
+                                 void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  CP_TRY(make_dims(shape, &d));
+  if (!a || !m || !mu || !core || !Gt || !w || !ws) return CP_EINVAL;
+  Layout L;
+  make_layout(d, CP_CORE_F64, 0, &L);
+  if (ws_bytes < L.total) return CP_ENOMEM;
+  Bufs B = carve(L, ws);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (info) CP_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+  CP_TRY(launch_gram(d, a, m, B.C, B.P, B.Gnm, B.Gall, nullptr, s));
+  CP_TRY(launch_mode_prep(d, B.C, B.Gnm, B.P, mu, Gt, B.U, B.LC, w, info, nullptr, s));
+  CP_TRY(launch_core_w(d, B.Gnm, B.LC, B.U, B.Wp, nullptr, s));
+  CP_TRY(launch_core_fill<double>(d, B.LC, B.U, B.Wp, core, nullptr, s));
+  return CP_OK;
+}
+
+extern "C" int cp_dgn_solve(const cp_shape* shape, const double* a, const double* mu, double* core,
+                            const double* w, double* f, int* info, void* ws, size_t ws_bytes,
+                            void* stream) {
+  Dims d;
+  CP_TRY(make_dims(shape, &d));
+  if (!a || !mu || !core || !w || !f || !info || !ws) return CP_EINVAL;
+  Layout L;
+  make_layout(d, CP_CORE_F64, 0, &L);
+  if (ws_bytes < L.total) return CP_ENOMEM;
+  Bufs B = carve(L, ws);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CP_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+  // S and K need the Gramians and the damped factors at (a, mu)
+  CP_TRY(launch_gram(d, a, nullptr, B.C, nullptr, B.Gnm, B.Gall, nullptr, s));
+  CP_TRY(launch_mode_prep(d, B.C, B.Gnm, B.P, mu, B.Gt, B.U, B.LC, nullptr, nullptr, nullptr, s));
+  CP_TRY(chol_factor<double>(core, d.ncore, info, nullptr, s));
+  CP_CUDA(cudaMemcpyAsync(B.w, w, d.ncore * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CP_TRY(solve_core(d, B, core, nullptr, CP_CORE_F64, 0, nullptr, s));
+  CP_CUDA(cudaMemcpyAsync(f, B.f, d.ncore * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return CP_OK;
+}
+
+extern "C" int cp_state_create(const cp_shape* shape, const cp_opts* opts, double* a, void* ws,
+                               size_t ws_bytes, cp_state** out) {
+  if (!opts || !a || !ws || !out) return CP_EINVAL;
+  Dims d;
+  CP_TRY(make_dims(shape, &d));
+  if (opts->core_mode != CP_CORE_F64 && opts->core_mode != CP_CORE_MIXED) return CP_EINVAL;
+  if (opts->max_iter < 0 || opts->refine_iters < 0 || opts->refine_iters > 64) return CP_EINVAL;
+  Layout L;
+  make_layout(d, opts->core_mode, 1, &L);
+  if (ws_bytes < L.total) return CP_ENOMEM;
+  cp_state* st = new (std::nothrow) cp_state;
+  if (!st) return CP_ENOMEM;
+  st->d = d;
+  st->o = *opts;
+  st->a = a;
+  st->ws = ws;
+  st->L = L;
+  st->B = carve(L, ws);
+  *out = st;
+  return CP_OK;
+}
+
+extern "C" int cp_state_destroy(cp_state* st) {
+  if (st) drop_graph(st);
+  delete st;
+  return CP_OK;
+}
+
+extern "C" cp_status* cp_state_status(cp_state* st) { return st ? st->B.status : nullptr; }
+
+extern "C" double* cp_state_buffer(cp_state* st, int id) {
+  if (!st) return nullptr;
+  switch (id) {
+    case 0: return st->B.m;
+    case 1: return st->B.delta;
+    case 2: return st->B.Gt;
+    case 3: return st->B.w;
+    case 4: return st->B.f;
+    case 5: return st->B.at;
+    default: return nullptr;
+  }
+}
+
+extern "C" int cp_state_init(cp_state* st, const void* Y, void* stream) {
+  if (!st || !Y) return CP_EINVAL;
+  const Dims& d = st->d;
+  const Bufs& B = st->B;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CP_CUDA(cudaMemsetAsync(B.m, 0, size_t(d.T) * d.R * sizeof(double), s));
+  CP_CUDA(cudaMemsetAsync(B.scal, 0, 64 * sizeof(double), s));
+  CP_CUDA(cudaMemsetAsync(B.info, 0, 64 * sizeof(int), s));
+  CP_TRY(launch_mttkrp(d, Y, st->a, B.m, B.scal + SC_R2, nullptr, s));
+  int64_t g = (d.J + 255) / 256;
+  if (g > 4 * kSMs) g = 4 * kSMs;
+  k_sumsq<<<unsigned(g), 256, 0, s>>>(Y, d.y_dtype, d.J, B.scal + SC_YN2);
+  CP_TRY(launch_gram(d, st->a, nullptr, B.C, nullptr, B.Gnm, B.Gall, nullptr, s));
+  k_init_status<<<1, 32, 0, s>>>(d, st->o, B.Gnm, B.scal, B.status, B.mu);
+  return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
+}
+
+extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
+  if (!st || !Y) return CP_EINVAL;
+  const Dims& d = st->d;
+  const Bufs& B = st->B;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int* skip = &B.status->stop;
+  const double* mu = &B.status->mu;
+  const int64_t nm = d.T * d.R;
+  k_step_begin<<<unsigned((nm + 255) / 256 < 64 ? (nm + 255) / 256 : 64), 256, 0, s>>>(nm, B.mt, B.scal,
+                                                                                       B.info);
+  CP_TRY(launch_gram(d, st->a, B.m, B.C, B.P, B.Gnm, B.Gall, skip, s));
+  CP_TRY(launch_mode_prep(d, B.C, B.Gnm, B.P, mu, B.Gt, B.U, B.LC, B.w, B.info + IN_INFO, skip, s));
+  CP_TRY(launch_core_w(d, B.Gnm, B.LC, B.U, B.Wp, skip, s));
+  if (st->o.core_mode == CP_CORE_F64) {
+    CP_TRY(launch_core_fill<double>(d, B.LC, B.U, B.Wp, B.core64, skip, s));
+    CP_TRY(chol_factor<double>(B.core64, d.ncore, B.info + IN_INFO, skip, s));
+    CP_TRY(solve_core(d, B, B.core64, nullptr, CP_CORE_F64, 0, skip, s));
+  } else {
+    CP_TRY(launch_core_fill<float>(d, B.LC, B.U, B.Wp, B.core32, skip, s));
+    CP_TRY(chol_factor<float>(B.core32, d.ncore, B.info + IN_INFO, skip, s));
+    CP_TRY(solve_core(d, B, nullptr, B.core32, CP_CORE_MIXED, st->o.refine_iters, skip, s));
+  }
+  const int64_t nupd = update_ctas(d);
+  k_update<<<unsigned(nupd), kUpdRows * 32, 0, s>>>(d, st->a, B.m, B.Gnm, B.Gt, B.f, mu, B.delta, B.at,
+                                                    B.part, skip);
+  CP_TRY(launch_mttkrp(d, Y, B.at, B.mt, B.scal + SC_R2T, skip, s));
+  k_control<<<1, 256, 0, s>>>(d, st->o, B.part, nupd, B.status, B.scal, B.info, B.scale);
+  int64_t gc = (nm + 255) / 256;
+  if (gc > 4 * kSMs) gc = 4 * kSMs;
+  k_commit<<<unsigned(gc), 256, 0, s>>>(d, B.info + IN_COMMIT, B.at, B.mt, B.scale, st->a, B.m);
+  return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
+}
+
+extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream);
+
+extern "C" int cp_state_capture(cp_state* st, const void* Y, int steps, void* stream) {
+  if (!st || !Y || steps < 1) return CP_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  drop_graph(st);
+  CP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = CP_OK;
+  for (int i = 0; i < steps && rc == CP_OK; ++i) rc = cp_dgn_step(st, Y, stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc != CP_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc != CP_OK ? rc : CP_ECUDA;
+  }
+  size_t nn = 0;
+  CP_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+  int kernels = 0;
+  if (nn) {
+    cudaGraphNode_t* nodes = new (std::nothrow) cudaGraphNode_t[nn];
+    if (!nodes) { cudaGraphDestroy(g); return CP_ENOMEM; }
+    if (cudaGraphGetNodes(g, nodes, &nn) == cudaSuccess) {
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
+    }
+    delete[] nodes;
+  }
+  cudaGraphExec_t x = nullptr;
+  if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return CP_ECUDA;
+  }
+  st->graph = g;
+  st->exec = x;
+  st->graph_steps = steps;
+  st->graph_kernels = kernels;
+  return CP_OK;
+}
+
+extern "C" int cp_state_launch(cp_state* st, void* stream) {
+  if (!st || !st->exec) return CP_EINVAL;
+  CP_CUDA(cudaGraphLaunch(st->exec, static_cast<cudaStream_t>(stream)));
+  return CP_OK;
+}
+
+extern "C" int cp_state_graph_kernels(cp_state* st) { return st ? st->graph_kernels : -1; }
