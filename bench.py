@@ -55,7 +55,39 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-extras", action="store_true",
                    help="only the timed steps (no float64 form, time-to-fit, oracle)")
+    p.add_argument("--profile", default="", choices=["", "mttkrp", "step"],
+                   help="profiling driver: run only this part (no JSON line)")
+    p.add_argument("--dims", default="", help="tensor dims for --profile, e.g. 400,400,400")
+    p.add_argument("--rank", type=int, default=R)
+    p.add_argument("--dtype", default="f32", choices=["f64", "f32", "bf16"])
     return p.parse_args()
+
+
+def run_profile(args):
+    """Run one part of the path a few times on a seeded device tensor (for ncu)."""
+    import torch
+    from paper_1205_2584_gb300 import cpdgn as cp
+    torch.cuda.set_device(0)
+    dims = tuple(int(x) for x in args.dims.split(",")) if args.dims else DIMS
+    g = torch.Generator(device="cuda").manual_seed(args.seed)
+    shape = cp.make_shape(dims, args.rank, args.dtype)
+    J = 1
+    for d in dims:
+        J *= d
+    Y = torch.randn(J, generator=g, device="cuda", dtype=torch.float32).to(cp.TORCH_DTYPE[shape.y_dtype])
+    a = torch.randn(args.rank * sum(dims), generator=g, device="cuda", dtype=torch.float64)
+    with torch.cuda.stream(torch.cuda.Stream()):
+        if args.profile == "mttkrp":
+            ws = cp.alloc_workspace(shape)
+            for _ in range(args.warmup + args.steps):
+                cp.mttkrp_all(shape, Y, a, ws=ws)
+        else:
+            st = cp.State(shape, a, mu0=-1.0, mu_max=float("inf"), max_iter=10 ** 9,
+                          core_mode=cp.CP_CORE_MIXED, refine_iters=8)
+            st.init(Y)
+            for _ in range(args.warmup + args.steps):
+                st.step(Y)
+        torch.cuda.synchronize()
 
 
 # ---------------------------------------------------------------------------
@@ -218,7 +250,7 @@ def _run_ours(args, rank, world, local):
     def new_state(shape, mode, a0, tol=0.0, max_iter=10 ** 9, mu_max=float("inf")):
         a = cp.factors_to_device(a0)
         st = cp.State(shape, a, mu0=-1.0, tau=1e-3, tol=tol, mu_max=mu_max, max_iter=max_iter,
-                      core_mode=mode, refine_iters=4)
+                      core_mode=mode, refine_iters=8)
         return st, a
 
     def timed_steps(st, Y, K, W):
@@ -253,7 +285,7 @@ def _run_ours(args, rank, world, local):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tensor pass, core factor) + f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R, "tensor_dtype": "f32",
-                      "core": "f32 Cholesky + f64 refinement (4 sweeps)", "l2": "flushed between steps",
+                      "core": "f32 Gauss-Jordan inverse + f64 refinement (<= 8 sweeps, adaptive)", "l2": "flushed between steps",
                       "parallelism": f"replicas x{world}", "global_batch": world},
            "gpu_launches": nk * args.steps, "clocks": clk.summary(),
            "state_after": {k: status[k] for k in ("iters", "accepted", "rel_err", "mu", "stop_reason",
@@ -281,7 +313,7 @@ def _run_ours(args, rank, world, local):
         mt_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
         bytes_alg = int(np.prod(DIMS)) * 4
         achieved = bytes_alg / (mt_ms * 1e-3) / 1e9
-        out["roofline"] = {"bound": "hbm", "kernel": "k_mttkrp<float,float,24> (MTTKRP + residual pass)",
+        out["roofline"] = {"bound": "hbm", "kernel": "k_mttkrp_tiled<float,float,24,1> (all-mode MTTKRP + residual pass)",
                            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                            "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": mt_ms,
@@ -385,7 +417,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile:
+        run_profile(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

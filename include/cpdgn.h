@@ -126,9 +126,12 @@ int cp_workspace_bytes(const cp_shape* shape, int core_mode, int what, size_t* b
  *                                                     no factor remains; the
  *                                                     diagonal n = m is Gamma^(n))
  *   Gamma_all   = Hadamard_k C^(k)                   (R x R)
- * Any output pointer may be NULL to skip it except C. */
+ * Gamma_nm and Gamma_all may be NULL to skip them.  Row blocks of every A^(n)
+ * are reduced on separate CTAs and summed in a fixed order in `ws`
+ * (cp_workspace_bytes(shape, 0, 0) bytes suffice), so the result is
+ * deterministic and C^(n) exactly symmetric. */
 int cp_gram(const cp_shape* shape, const double* a, double* C, double* Gamma_nm,
-            double* Gamma_all, void* stream);
+            double* Gamma_all, void* ws, size_t ws_bytes, void* stream);
 
 /* All-mode MTTKRP in one pass over Y (Algorithm 1 step 6, Sec. 4.6 Eq. mappingJ):
  *   m = [vec M_1; ...; vec M_N],  M_n = Y_(n) (A^(N) (.) ... A^(n+1) (.) A^(n-1) (.) ... A^(1)),
@@ -160,10 +163,11 @@ int cp_dgn_core_build(const cp_shape* shape, const double* a, const double* m,
                       void* ws, size_t ws_bytes, void* stream);
 
 /* Solve the core system built by cp_dgn_core_build for f = B_mu w
- * (Theorem 1, Eq. inverse_f1a):  f = K w - K S core^{-1} S^T K w.
- * core (in/out): on return holds its lower Cholesky factor (float64).  info
- * (device int) receives 0, or the 1-based index of the first non-positive
- * pivot.  a and mu must be those given to cp_dgn_core_build. */
+ * (Theorem 1, Eq. inverse_f1a):  f = K w - K S core^{-1} S^T K w, by float64
+ * Cholesky.  core (in/out): on return holds its lower Cholesky factor (the
+ * upper triangle is left unspecified).  info (device int) receives 0, or the
+ * 1-based index of the first non-positive pivot.  a and mu must be those
+ * given to cp_dgn_core_build. */
 int cp_dgn_solve(const cp_shape* shape, const double* a, const double* mu, double* core,
                  const double* w, double* f, int* info, void* ws, size_t ws_bytes,
                  void* stream);

@@ -66,7 +66,7 @@ assert ctypes.sizeof(Status) == 128
 _vp, _sz = ctypes.c_void_p, ctypes.c_size_t
 _sig = {
     "cp_workspace_bytes": [ctypes.POINTER(Shape), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_sz)],
-    "cp_gram": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp],
+    "cp_gram": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _sz, _vp],
     "cp_mttkrp_all": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _sz, _vp],
     "cp_fit": [ctypes.POINTER(Shape), _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _sz, _vp],
     "cp_dgn_core_build": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
@@ -154,13 +154,14 @@ def tensor_to_device(Y, y_dtype: str, device="cuda") -> torch.Tensor:
 # stand-alone calls
 # ---------------------------------------------------------------------------
 
-def gram(shape: Shape, a: torch.Tensor, stream=None):
+def gram(shape: Shape, a: torch.Tensor, ws=None, stream=None):
     N, R = shape.N, shape.R
     C = torch.empty(N * R * R, dtype=torch.float64, device=a.device)
     Gnm = torch.empty(N * N * R * R, dtype=torch.float64, device=a.device)
     Gall = torch.empty(R * R, dtype=torch.float64, device=a.device)
-    _check(_lib.cp_gram(ctypes.byref(shape), _ptr(a), _ptr(C), _ptr(Gnm), _ptr(Gall), _stream(stream)),
-           "cp_gram")
+    ws = ws if ws is not None else alloc_workspace(shape, device=a.device)
+    _check(_lib.cp_gram(ctypes.byref(shape), _ptr(a), _ptr(C), _ptr(Gnm), _ptr(Gall), _ptr(ws), ws.numel(),
+                        _stream(stream)), "cp_gram")
     return C, Gnm, Gall
 
 
@@ -217,7 +218,7 @@ class State:
 
     def __init__(self, shape: Shape, a: torch.Tensor, *, mu0: float = -1.0, tau: float = 1e-3,
                  tol: float = 0.0, mu_max: float = 1e30, max_iter: int = 1000, normalize: bool = True,
-                 core_mode: int = CP_CORE_F64, refine_iters: int = 4):
+                 core_mode: int = CP_CORE_F64, refine_iters: int = 8):
         assert a.dtype == torch.float64 and a.is_cuda and a.is_contiguous()
         self.shape = shape
         self.a = a

@@ -81,8 +81,9 @@ enum Seg {
   S_D,            // N R^2     refinement correction
   S_F,            // N R^2     f
   S_WP,           // N(N-1)/2 R^3   W_(n,m) of the core build
-  S_CORE32,       // (N R^2)^2 float  (mixed mode)
-  S_VEC32,        // 2 N R^2 float    (mixed-mode triangular solves)
+  S_CORE32,       // 2 (N R^2)^2 float  (mixed mode: core and its Gauss-Jordan partner)
+  S_GPART,        // partial sums of the Gram kernel
+  S_PINV,         // 2 x 64 x 64 float: pivot inverses of the Gauss-Jordan sweeps
   S_PART,         // partial sums of the update kernel
   S_SCAL,         // small scalars and flags (doubles)
   S_INFO,         // ints
@@ -119,8 +120,13 @@ inline void make_layout(const Dims& d, int core_mode, int with_state, Layout* L)
   sz[S_P] = sz[S_LC] = sz[S_U] = sz[S_GT] = d.N * d.RR * dbl;
   sz[S_W] = sz[S_KW] = sz[S_B] = sz[S_Y] = sz[S_Z] = sz[S_RES] = sz[S_D] = sz[S_F] = nr2 * dbl;
   sz[S_WP] = size_t(d.N) * (d.N - 1) / 2 * d.RR * d.R * dbl;
-  sz[S_CORE32] = (core_mode == CP_CORE_MIXED) ? nr2 * nr2 * sizeof(float) : 0;
-  sz[S_VEC32] = 2 * nr2 * sizeof(float);
+  sz[S_CORE32] = (core_mode == CP_CORE_MIXED) ? 2 * nr2 * nr2 * sizeof(float) : 0;
+  {
+    size_t ch = 0;
+    for (int n = 0; n < d.N; ++n) ch += size_t((d.I[n] + 7) / 8);
+    sz[S_GPART] = ch * size_t(d.R * (d.R + 1) / 2 + d.RR) * dbl;   // kGramRows = 8
+  }
+  sz[S_PINV] = 2 * 64 * 64 * sizeof(float);
   sz[S_PART] = size_t(update_ctas(d)) * (1 + d.R) * dbl;
   sz[S_SCAL] = 64 * dbl;
   sz[S_INFO] = 64 * sizeof(int);

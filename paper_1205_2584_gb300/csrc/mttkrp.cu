@@ -226,6 +226,298 @@ __global__ void __launch_bounds__(kMtThreads) k_mttkrp(MttkrpParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// k_mttkrp_tiled: the production pass (I_1 <= 256 * RPT).
+//
+// Per tile of TF fibres (double-buffered in shared memory with cp.async):
+//   phase B: thread = row i (RPT rows), all fibres of the tile:
+//            M_1[i] += y[i,f] kr_f,  e = y[i,f] - A1[i] . kr_f,  e2 += e^2
+//            (per fibre: R/4 broadcast 16-byte loads of kr_f feed 2R FMAs)
+//   phase A: t_f = A1^T y_f as 4 x 4 register blocks of (f, r) with the
+//            I_1 sum split into segments, then the segments summed
+//   phase D: M_n[i_n(f)] += t_f * loo_f(n) for n >= 2: mode 2 directly
+//            (fibres of a tile have distinct i_2 when TF <= I_2), modes >= 3
+//            by one thread per (n, r) scanning the tile's fibres in order.
+// ---------------------------------------------------------------------------
+constexpr int kT2 = 256;          // threads
+constexpr int kSeg = 8;           // segments of the I_1 sum in phase A
+
+struct Tiled {
+  Dims d;
+  const void* Y;
+  const double* a;
+  double* m;
+  double* resid2;
+  const int* skip;
+  int64_t fib_per_cta;
+  int TF, ldy, Rp;                // fibres per tile, tile leading dim, R padded to 4
+  int64_t mn_elems;               // sum_{n>=2} I_n R
+};
+
+template <typename TY>
+__device__ __forceinline__ void cp_async_elem(TY* dst, const TY* src);
+template <>
+__device__ __forceinline__ void cp_async_elem<float>(float* dst, const float* src) {
+  unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+}
+template <>
+__device__ __forceinline__ void cp_async_elem<double>(double* dst, const double* src) {
+  unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ double to_f(double x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Copy nf fibres starting at fibre f0 into the tile buffer (row f at f * ldy).
+template <typename TY>
+__device__ void tile_copy(const TY* Y, int64_t f0, int nf, int I1, int ldy, TY* dst) {
+  const int tot = nf * I1;
+  const int64_t base = f0 * I1;
+  int f = 0, i = threadIdx.x;
+  while (i >= I1 && f < nf) { i -= I1; ++f; }
+  for (int e = threadIdx.x; e < tot; e += kT2) {
+    if constexpr (sizeof(TY) == 2) {
+      dst[f * ldy + i] = Y[base + e];
+    } else {
+      cp_async_elem<TY>(dst + f * ldy + i, Y + base + e);
+    }
+    i += kT2;
+    while (i >= I1) { i -= I1; ++f; }
+  }
+}
+
+template <typename TY, typename TA, int RMAX, int RPT>
+__global__ void __launch_bounds__(kT2) k_mttkrp_tiled(Tiled p) {
+  if (p.skip && *p.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims& d = p.d;
+  const int R = d.R, N = d.N, Rp = p.Rp;
+  const int I1 = int(d.I[0]);
+  const int TF = p.TF, ldy = p.ldy;
+  const int tid = threadIdx.x;
+  const bool want_m = p.m != nullptr;
+
+  TA* A1s = reinterpret_cast<TA*>(smem_raw);                         // I1 x Rp row-major
+  TA* krs = A1s + size_t(I1) * Rp;                                    // TF x Rp
+  TA* ts = krs + size_t(TF) * Rp;                                     // kSeg x TF x Rp partials
+  TA* loos = ts + size_t(kSeg) * TF * Rp;                             // (N-1) x TF x Rp
+  TA* Mns = loos + size_t(N - 1) * TF * Rp;                           // mn_elems
+  TY* Yt0 = reinterpret_cast<TY*>(Mns + p.mn_elems);                  // 2 x TF x ldy
+  TY* Yt1 = Yt0 + size_t(TF) * ldy;
+  int* fidx = reinterpret_cast<int*>(Yt1 + size_t(TF) * ldy + 8);     // TF x CP_MAX_N
+  double* red = reinterpret_cast<double*>(
+      (reinterpret_cast<uintptr_t>(fidx + TF * CP_MAX_N) + 15) & ~uintptr_t(15));
+
+  const double* a = p.a;
+  for (int e = tid; e < I1 * Rp; e += kT2) {
+    const int i = e / Rp, r = e % Rp;
+    A1s[e] = (r < R) ? TA(a[i + int64_t(r) * I1]) : TA(0);
+  }
+  for (int64_t e = tid; e < p.mn_elems; e += kT2) Mns[e] = TA(0);
+  int64_t mn_off[CP_MAX_N];
+  {
+    int64_t o = 0;
+    for (int n = 1; n < N; ++n) { mn_off[n] = o; o += d.I[n] * R; }
+  }
+  const int64_t f_begin = int64_t(blockIdx.x) * p.fib_per_cta;
+  const int64_t f_end = (f_begin + p.fib_per_cta < d.nfib) ? f_begin + p.fib_per_cta : d.nfib;
+  const TY* Y = reinterpret_cast<const TY*>(p.Y);
+
+  TA acc[RPT][RMAX];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q)
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) acc[q][r] = TA(0);
+  double e2_total = 0.0;
+
+  if (f_begin < f_end) {
+    const int nf0 = int((f_end - f_begin) < TF ? (f_end - f_begin) : TF);
+    tile_copy<TY>(Y, f_begin, nf0, I1, ldy, Yt0);
+  }
+  cp_async_commit();
+  int buf = 0;
+  for (int64_t f0 = f_begin; f0 < f_end; f0 += TF) {
+    const int nf = int((f_end - f0) < TF ? (f_end - f0) : TF);
+    TY* Ycur = buf ? Yt1 : Yt0;
+    TY* Ynext = buf ? Yt0 : Yt1;
+    // prefetch the next tile
+    const int64_t f1 = f0 + TF;
+    if (f1 < f_end) {
+      const int nf1 = int((f_end - f1) < TF ? (f_end - f1) : TF);
+      tile_copy<TY>(Y, f1, nf1, I1, ldy, Ynext);
+    }
+    cp_async_commit();
+    // fibre multi-indices (i_2..i_N) of this tile
+    for (int f = tid; f < nf; f += kT2) {
+      int64_t rem = f0 + f;
+#pragma unroll
+      for (int k = 1; k < CP_MAX_N; ++k) {
+        if (k < N) {
+          fidx[f * CP_MAX_N + k] = int(rem % d.I[k]);
+          rem /= d.I[k];
+        }
+      }
+    }
+    __syncthreads();
+    // Khatri-Rao rows and leave-one-out products
+    for (int e = tid; e < nf * Rp; e += kT2) {
+      const int f = e / Rp, r = e % Rp;
+      TA v[CP_MAX_N];
+#pragma unroll
+      for (int k = 1; k < CP_MAX_N; ++k)
+        if (k < N) v[k] = (r < R) ? TA(a[d.aoff[k] + fidx[f * CP_MAX_N + k] + int64_t(r) * d.I[k]]) : TA(0);
+      TA kr = TA(1);
+#pragma unroll
+      for (int k = 1; k < CP_MAX_N; ++k)
+        if (k < N) kr *= v[k];
+      krs[f * Rp + r] = (r < R) ? kr : TA(0);
+      if (want_m) {
+#pragma unroll
+        for (int n = 1; n < CP_MAX_N; ++n) {
+          if (n < N) {
+            TA lo = TA(1);
+#pragma unroll
+            for (int k = 1; k < CP_MAX_N; ++k)
+              if (k < N && k != n) lo *= v[k];
+            loos[(size_t(n - 1) * TF + f) * Rp + r] = lo;
+          }
+        }
+      }
+    }
+    cp_async_wait<1>();
+    __syncthreads();
+    // phase B: rows
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int i = tid + q * kT2;
+      if (i < I1) {
+        TA arow[RMAX];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) arow[r] = (r < Rp) ? A1s[i * Rp + r] : TA(0);
+        TA e2 = TA(0);
+        for (int f = 0; f < nf; ++f) {
+          const TA y = TA(to_f(Ycur[f * ldy + i]));
+          const TA* kf = krs + f * Rp;
+          TA yh0 = TA(0), yh1 = TA(0);
+#pragma unroll
+          for (int r = 0; r < RMAX; r += 2) {
+            if (r < Rp) {     // Rp is a multiple of 4: pairs are whole
+              const TA k0 = kf[r], k1 = kf[r + 1];
+              acc[q][r] = fma(y, k0, acc[q][r]);
+              acc[q][r + 1] = fma(y, k1, acc[q][r + 1]);
+              yh0 = fma(arow[r], k0, yh0);
+              yh1 = fma(arow[r + 1], k1, yh1);
+            }
+          }
+          const TA e = y - (yh0 + yh1);
+          e2 = fma(e, e, e2);
+        }
+        e2_total += double(e2);
+      }
+    }
+    // phase A: t_f partials over kSeg segments of rows, 4 x 4 blocks
+    if (want_m) {
+      const int nfb = (nf + 3) / 4, nrb = Rp / 4;
+      const int seg_len = (I1 + kSeg - 1) / kSeg;
+      for (int task = tid; task < nfb * nrb * kSeg; task += kT2) {
+        const int rb = task % nrb, fb = (task / nrb) % nfb, sg = task / (nrb * nfb);
+        const int ib = sg * seg_len, ie = (ib + seg_len < I1) ? ib + seg_len : I1;
+        TA c[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) c[u][v] = TA(0);
+        const int fr = fb * 4;
+        for (int i = ib; i < ie; ++i) {
+          TA yv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) yv[u] = (fr + u < nf) ? TA(to_f(Ycur[(fr + u) * ldy + i])) : TA(0);
+          const TA* ar = A1s + i * Rp + rb * 4;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const TA av = ar[v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c[u][v] = fma(yv[u], av, c[u][v]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) ts[(size_t(sg) * TF + fr + u) * Rp + rb * 4 + v] = c[u][v];
+      }
+    }
+    __syncthreads();
+    if (want_m) {
+      // sum the segments: ts[0] <- sum_sg ts[sg]
+      for (int e = tid; e < nf * Rp; e += kT2) {
+        TA s = ts[e];
+#pragma unroll
+        for (int sg = 1; sg < kSeg; ++sg) s += ts[size_t(sg) * TF * Rp + e];
+        ts[e] = s;
+      }
+      __syncthreads();
+      // phase D, mode 2: distinct i_2 inside the tile when TF <= I_2
+      const bool direct2 = TF <= d.I[1];
+      if (direct2) {
+        for (int e = tid; e < nf * R; e += kT2) {
+          const int f = e / R, r = e % R;
+          const int i2 = fidx[f * CP_MAX_N + 1];
+          Mns[mn_off[1] + int64_t(i2) * R + r] += ts[f * Rp + r] * loos[(size_t(0) * TF + f) * Rp + r];
+        }
+      }
+      // modes >= 3 (and mode 2 otherwise): one thread per (n, r), fibres in order
+      const int n_lo = direct2 ? 2 : 1;
+      for (int task = tid; task < (N - n_lo) * R; task += kT2) {
+        const int n = n_lo + task / R, r = task % R;
+        int cur = fidx[0 * CP_MAX_N + n];
+        TA s = TA(0);
+        for (int f = 0; f < nf; ++f) {
+          const int in = fidx[f * CP_MAX_N + n];
+          if (in != cur) {
+            Mns[mn_off[n] + int64_t(cur) * R + r] += s;
+            s = TA(0);
+            cur = in;
+          }
+          s = fma(ts[f * Rp + r], loos[(size_t(n - 1) * TF + f) * Rp + r], s);
+        }
+        Mns[mn_off[n] + int64_t(cur) * R + r] += s;
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  cp_async_wait<0>();
+  // flush
+  if (want_m) {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int i = tid + q * kT2;
+      if (i < I1) {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) atomicAdd(&p.m[i + int64_t(r) * I1], double(acc[q][r]));
+      }
+    }
+    for (int n = 1; n < N; ++n) {
+      const int In = int(d.I[n]);
+      for (int e = tid; e < In * R; e += kT2) {
+        const int i = e % In, r = e / In;
+        atomicAdd(&p.m[d.aoff[n] + i + int64_t(r) * In], double(Mns[mn_off[n] + int64_t(i) * R + r]));
+      }
+    }
+  }
+  if (p.resid2) {
+    const double sum = block_sum<kT2>(e2_total, red);
+    if (tid == 0) atomicAdd(p.resid2, sum);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static int rmax_for(int R) {
@@ -266,16 +558,102 @@ static size_t mttkrp_smem(const Dims& d, int TF, int I1p, int mn_in_smem, size_t
   return bytes;
 }
 
+template <typename TY, typename TA, int RMAX, int RPT>
+static int launch_tiled_t(const Tiled& p, int grid, size_t smem, cudaStream_t s) {
+  auto kern = k_mttkrp_tiled<TY, TA, RMAX, RPT>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    return CP_ECUDA;
+  kern<<<grid, kT2, smem, s>>>(p);
+  return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
+}
+
+template <typename TY, typename TA, int RPT>
+static int launch_tiled_r(const Tiled& p, int grid, size_t smem, cudaStream_t s) {
+  switch (rmax_for(p.d.R)) {
+    case 4: return launch_tiled_t<TY, TA, 4, RPT>(p, grid, smem, s);
+    case 8: return launch_tiled_t<TY, TA, 8, RPT>(p, grid, smem, s);
+    case 16: return launch_tiled_t<TY, TA, 16, RPT>(p, grid, smem, s);
+    case 24: return launch_tiled_t<TY, TA, 24, RPT>(p, grid, smem, s);
+    default: return launch_tiled_t<TY, TA, 32, RPT>(p, grid, smem, s);
+  }
+}
+
+template <typename TY, typename TA>
+static int launch_tiled_q(const Tiled& p, int grid, size_t smem, cudaStream_t s) {
+  const int I1 = int(p.d.I[0]);
+  if (I1 <= kT2) return launch_tiled_r<TY, TA, 1>(p, grid, smem, s);
+  if (I1 <= 2 * kT2) return launch_tiled_r<TY, TA, 2>(p, grid, smem, s);
+  return launch_tiled_r<TY, TA, 3>(p, grid, smem, s);
+}
+
+static size_t tiled_smem(const Dims& d, int TF, int ldy, int Rp, size_t ta, size_t ty) {
+  const size_t mn = size_t(d.T - d.I[0]) * d.R;
+  size_t e = size_t(d.I[0]) * Rp + size_t(TF) * Rp * (1 + kSeg + (d.N - 1)) + mn;
+  return e * ta + 2 * size_t(TF) * ldy * ty + 8 * 8 + size_t(TF) * CP_MAX_N * sizeof(int) + 16 +
+         kT2 * sizeof(double) + 16;
+}
+
 // Enqueue one pass (m and resid2 must already be zeroed).
 int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, double* resid2,
                   const int* skip, cudaStream_t s) {
   const size_t ta = (d.y_dtype == CP_F64) ? sizeof(double) : sizeof(float);
+  const size_t ty = (d.y_dtype == CP_F64) ? 8 : (d.y_dtype == CP_F32 ? 4 : 2);
+  const int I1 = int(d.I[0]);
+  const size_t max_smem = 220 * 1024;
+  if (I1 <= 3 * kT2) {
+    const int Rp = (d.R + 3) / 4 * 4;
+    // fibres per tile: about 16 KB of tensor per buffer, 4..64, and <= I_2 when possible
+    int TF = int(16384 / (size_t(I1) * ty));
+    if (TF > 64) TF = 64;
+    if (TF < 4) TF = 4;
+    TF &= ~3;                                    // phase A works on blocks of 4 fibres
+    // leading dimension: odd in 4-byte words (conflict-free strided reads)
+    int ldy = I1;
+    if (ty == 4 || ty == 8) {
+      if (ldy % 2 == 0) ldy += 1;              // odd: fibre rows fall in distinct banks
+    } else {
+      ldy += ((2 - ldy % 4) + 4) % 4;          // 2 mod 4 bf16 elements = odd 4-byte words
+    }
+    size_t smem = tiled_smem(d, TF, ldy, Rp, ta, ty);
+    while (smem > max_smem && TF > 4) {
+      TF = (TF / 2) & ~3;
+      if (TF < 4) TF = 4;
+      smem = tiled_smem(d, TF, ldy, Rp, ta, ty);
+    }
+    if (smem <= max_smem) {
+      int per_sm = int((228 * 1024) / (smem + 1024));
+      if (per_sm < 1) per_sm = 1;
+      if (per_sm > 4) per_sm = 4;
+      const int64_t ntiles = (d.nfib + TF - 1) / TF;
+      int64_t grid = int64_t(kSMs) * per_sm;
+      if (grid > ntiles) grid = ntiles;
+      if (grid < 1) grid = 1;
+      const int64_t tiles_per = (ntiles + grid - 1) / grid;
+      Tiled p;
+      p.d = d;
+      p.Y = Y;
+      p.a = a;
+      p.m = m;
+      p.resid2 = resid2;
+      p.skip = skip;
+      p.fib_per_cta = tiles_per * TF;
+      p.TF = TF;
+      p.ldy = ldy;
+      p.Rp = Rp;
+      p.mn_elems = int64_t(d.T - d.I[0]) * d.R;
+      grid = (d.nfib + p.fib_per_cta - 1) / p.fib_per_cta;
+      switch (d.y_dtype) {
+        case CP_F64: return launch_tiled_q<double, double>(p, int(grid), smem, s);
+        case CP_F32: return launch_tiled_q<float, float>(p, int(grid), smem, s);
+        default: return launch_tiled_q<__nv_bfloat16, float>(p, int(grid), smem, s);
+      }
+    }
+  }
+  // general fallback: one CTA tile of whole fibres (any I_1 that fits)
   int TF = kMtThreads / d.R;
   if (TF > 32) TF = 32;
   if (TF < 1) TF = 1;
-  const int I1 = int(d.I[0]);
-  const int I1p = I1 + ((ta == 4) ? 1 : 1);
-  const size_t max_smem = 220 * 1024;
+  const int I1p = I1 + 1;
   int mn_in_smem = 1;
   size_t smem = mttkrp_smem(d, TF, I1p, 1, ta);
   if (smem > max_smem) {
@@ -286,8 +664,7 @@ int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, doub
     TF /= 2;
     smem = mttkrp_smem(d, TF, I1p, 0, ta);
   }
-  if (smem > max_smem) return CP_EINVAL;   // I_1 * R too large for one CTA's tile
-  // CTAs resident per SM given the shared-memory footprint
+  if (smem > max_smem) return CP_EINVAL;
   int per_sm = int((228 * 1024) / (smem + 1024));
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 4) per_sm = 4;

@@ -25,44 +25,49 @@ namespace cpdgn {
 
 int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, double* resid2,
                   const int* skip, cudaStream_t s);
-int launch_gram(const Dims& d, const double* a, const double* m, double* C, double* P,
+int launch_gram(const Dims& d, const double* a, const double* m, double* part, double* C, double* P,
                 double* Gnm, double* Gall, const int* skip, cudaStream_t s);
-int launch_mode_prep(const Dims& d, const double* C, const double* Gnm, const double* P,
-                     const double* mu, double* Gt, double* U, double* LC, double* w, int* info,
-                     const int* skip, cudaStream_t s);
+int launch_mode_prep(const Dims& d, const double* C, const double* P, const double* mu, double* Gnm,
+                     double* Gt, double* U, double* LC, double* w, int* info, const int* skip,
+                     cudaStream_t s);
 int launch_core_w(const Dims& d, const double* Gnm, const double* LC, const double* U, double* Wp,
                   const int* skip, cudaStream_t s);
 template <typename T>
-int launch_core_fill(const Dims& d, const double* LC, const double* U, const double* Wp, T* core,
+int launch_core_fill(const Dims& d, const double* LC, const double* U, const double* Wp, T* core, int full,
                      const int* skip, cudaStream_t s);
 int launch_apply_K(const Dims& d, const double* Gnm, const double* x, const double* base, double* out,
                    const int* skip, cudaStream_t s);
 int launch_apply_S(const Dims& d, const double* LC, const double* U, const double* x, double* out,
                    const int* skip, cudaStream_t s);
-int launch_apply_ST(const Dims& d, const double* LC, const double* U, const double* Gnm,
-                    const double* x, int kx, const double* b, const double* y, double* out,
+int launch_apply_ST(const Dims& d, const double* LC, const double* U, const double* Gnm, const double* x,
+                    int kx, const double* b, const double* y, double* out, double* kw, double* norm2,
                     const int* skip, cudaStream_t s);
 template <typename T>
 int chol_factor(T* A, int64_t n, int* info, const int* skip, cudaStream_t s);
 template <typename T, typename TX>
 int chol_solve(const T* L, int64_t n, TX* x, TX* tmp, TX* y, const int* skip, cudaStream_t s);
+template <typename T>
+int gj_invert(T* A, T* B, T* pinv, int64_t n, int* info, const int* skip, cudaStream_t s, T** result);
+int launch_gemv_acc(const float* X, int64_t n, const double* r, double* y, const double* b2, const double* r2,
+                    const double* r2prev, int* done, double tol2, const int* skip, cudaStream_t s);
 
 // scalar slots (doubles) inside S_SCAL
-enum { SC_R2T = 0, SC_YN2 = 1, SC_R2 = 2, SC_REFN = 3, SC_BN = 4 };
+enum { SC_R2T = 0, SC_YN2 = 1, SC_R2 = 2, SC_REFN = 3, SC_NRM = 8 };   // SC_NRM..: ||b||^2, ||res_k||^2
+constexpr int kMaxRefine = 48;
 // int slots inside S_INFO
-enum { IN_INFO = 0, IN_COMMIT = 1, IN_ZERO = 2 };
+enum { IN_INFO = 0, IN_COMMIT = 1, IN_ZERO = 2, IN_RDONE = 3 };
 
 struct Bufs {
   double *C, *Gnm, *Gall, *P, *LC, *U, *Gt, *w, *Kw, *b, *y, *Z, *res, *dcor, *f, *Wp;
-  float *core32, *vec32;
-  double *part, *scal;
+  float *core32, *core32b, *pinv;
+  double *gpart, *part, *scal;
   int* info;
   cp_status* status;
   double *m, *mt, *at, *delta, *scale, *mu;
   double* core64;
 };
 
-static Bufs carve(const Layout& L, void* ws) {
+static Bufs carve(const Layout& L, void* ws, int64_t ncore) {
   char* base = static_cast<char*>(ws);
   Bufs b;
   b.C = reinterpret_cast<double*>(base + L.off[S_C]);
@@ -82,7 +87,9 @@ static Bufs carve(const Layout& L, void* ws) {
   b.f = reinterpret_cast<double*>(base + L.off[S_F]);
   b.Wp = reinterpret_cast<double*>(base + L.off[S_WP]);
   b.core32 = reinterpret_cast<float*>(base + L.off[S_CORE32]);
-  b.vec32 = reinterpret_cast<float*>(base + L.off[S_VEC32]);
+  b.core32b = b.core32 + size_t(0);   // set by carve_core2()
+  b.gpart = reinterpret_cast<double*>(base + L.off[S_GPART]);
+  b.pinv = reinterpret_cast<float*>(base + L.off[S_PINV]);
   b.part = reinterpret_cast<double*>(base + L.off[S_PART]);
   b.scal = reinterpret_cast<double*>(base + L.off[S_SCAL]);
   b.info = reinterpret_cast<int*>(base + L.off[S_INFO]);
@@ -94,6 +101,7 @@ static Bufs carve(const Layout& L, void* ws) {
   b.scale = reinterpret_cast<double*>(base + L.off[S_SCALE]);
   b.mu = reinterpret_cast<double*>(base + L.off[S_MU]);
   b.core64 = reinterpret_cast<double*>(base + L.off[S_CORE64]);
+  b.core32b = b.core32 + size_t(ncore) * size_t(ncore);
   return b;
 }
 
@@ -101,38 +109,15 @@ static Bufs carve(const Layout& L, void* ws) {
 // small kernels
 // ---------------------------------------------------------------------------
 
-// vec32 <- float(src)   or   dst (+)= double(vec32)
-__global__ void k_cvt(int64_t n, const double* src, float* x32, const float* y32, double* dst,
-                      int accumulate, const int* skip) {
-  if (skip && *skip) return;
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (src) x32[i] = float(src[i]);
-  if (dst) dst[i] = accumulate ? dst[i] + double(y32[i]) : double(y32[i]);
-}
-
-// relative residual ||res|| / ||b|| of the last refinement sweep -> scal[SC_REFN]
-__global__ void k_refine_norm(int64_t n, const double* res, const double* b, double* scal,
-                              const int* skip) {
-  if (skip && *skip) return;
-  __shared__ double sh[256];
-  double sr = 0, sb = 0;
-  for (int64_t i = threadIdx.x; i < n; i += 256) {
-    sr = fma(res[i], res[i], sr);
-    sb = fma(b[i], b[i], sb);
-  }
-  const double tr = block_sum<256>(sr, sh);
-  const double tb = block_sum<256>(sb, sh);
-  if (threadIdx.x == 0) scal[SC_REFN] = (tb > 0) ? sqrt(tr / tb) : 0.0;
-}
-
-__global__ void k_step_begin(int64_t nm, double* mt, double* scal, int* info) {
+__global__ void k_step_begin(int64_t nm, double* mt, double* scal, int* info, const cp_status* st) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i == 0) {
     info[IN_INFO] = 0;
     info[IN_COMMIT] = 0;
+    info[IN_RDONE] = (st->stop != CP_RUNNING) ? 1 : 0;
     scal[SC_R2T] = 0.0;
   }
+  if (i < kMaxRefine + 2) scal[SC_NRM + i] = 0.0;
   for (; i < nm; i += int64_t(gridDim.x) * blockDim.x) mt[i] = 0.0;
 }
 
@@ -245,7 +230,15 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
     st->denom = den;
     st->resid2_trial = r2t;
     st->info = bad;
-    st->refine_resid = scal[SC_REFN];
+    {
+      double rr = 0.0;   // relative residual of the last refinement sweep that ran
+      for (int k = kMaxRefine; k >= 1; --k)
+        if (scal[SC_NRM + k] > 0.0) {
+          rr = sqrt(scal[SC_NRM + k] / scal[SC_NRM]);
+          break;
+        }
+      st->refine_resid = rr;
+    }
     st->mu = mu;
     st->nu = nu;
     st->last_accepted = accept ? 1 : 0;
@@ -341,35 +334,32 @@ __global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double
 // shared pieces of the core solve
 // ---------------------------------------------------------------------------
 
-// f = K w - K S y with y = core^{-1} S^T K w, given factorised core.
-// mode CP_CORE_F64: L64 holds the float64 factor; CP_CORE_MIXED: L32 holds the
-// float32 factor and the solution is refined with the float64 operator.
-static int solve_core(const Dims& d, const Bufs& B, const double* L64, const float* L32, int mode,
+// f = K w - K S y with y = core^{-1} b, b = S^T K w.
+// CP_CORE_F64: L64 holds the float64 Cholesky factor, two triangular solves.
+// CP_CORE_MIXED: X32 holds the float32 inverse of the core; y = X b, then up
+// to refine_iters sweeps y += X (b - y - S^T K S y) with the float64
+// operator, stopping once ||b - core y|| <= 1e-15 ||b|| or the residual stops
+// shrinking (kernels of later sweeps return at once; the graph is fixed).
+static int solve_core(const Dims& d, const Bufs& B, const double* L64, const float* X32, int mode,
                       int refine_iters, const int* skip, cudaStream_t s) {
   const int64_t n = d.ncore;
-  CP_TRY(launch_apply_K(d, B.Gnm, B.w, nullptr, B.Kw, skip, s));                  // Kw
-  CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Kw, 0, nullptr, nullptr, B.b, skip, s));  // b = S^T K w
-  const unsigned g = unsigned((n + 255) / 256);
+  double* nrm = B.scal + SC_NRM;
+  // b = S^T (K w), ||b||^2, and K w kept for the last line
+  CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.w, 1, nullptr, nullptr, B.b, B.Kw, nrm, skip, s));
   if (mode == CP_CORE_F64) {
     CP_CUDA(cudaMemcpyAsync(B.res, B.b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CP_TRY((chol_solve<double, double>(L64, n, B.res, B.dcor, B.y, skip, s)));
   } else {
-    float* x32 = B.vec32;
-    float* t32 = B.vec32 + n;
-    // y = core32^{-1} b, then y += core32^{-1} (b - y - S^T K S y), refine_iters times
-    k_cvt<<<g, 256, 0, s>>>(n, B.b, x32, nullptr, nullptr, 0, skip);
-    CP_TRY((chol_solve<float, float>(L32, n, x32, t32, x32, skip, s)));
-    k_cvt<<<g, 256, 0, s>>>(n, nullptr, nullptr, x32, B.y, 0, skip);
-    for (int it = 0; it < refine_iters; ++it) {
-      CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, skip, s));
-      CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Z, 1, B.b, B.y, B.res, skip, s));
-      k_cvt<<<g, 256, 0, s>>>(n, B.res, x32, nullptr, nullptr, 0, skip);
-      CP_TRY((chol_solve<float, float>(L32, n, x32, t32, x32, skip, s)));
-      k_cvt<<<g, 256, 0, s>>>(n, nullptr, nullptr, x32, B.y, 1, skip);
+    int* rdone = B.info + IN_RDONE;
+    const int K = refine_iters < kMaxRefine ? refine_iters : kMaxRefine;
+    CP_CUDA(cudaMemsetAsync(B.y, 0, n * sizeof(double), s));
+    CP_TRY(launch_gemv_acc(X32, n, B.b, B.y, nullptr, nullptr, nullptr, nullptr, 0.0, skip, s));
+    for (int it = 1; it <= K; ++it) {
+      CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, rdone, s));
+      CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Z, 1, B.b, B.y, B.res, nullptr, nrm + it, rdone, s));
+      CP_TRY(launch_gemv_acc(X32, n, B.res, B.y, nrm, nrm + it, it > 1 ? nrm + it - 1 : nullptr, rdone, 1e-30,
+                             rdone, s));
     }
-    CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, skip, s));
-    CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Z, 1, B.b, B.y, B.res, skip, s));
-    k_refine_norm<<<1, 256, 0, s>>>(n, B.res, B.b, B.scal, skip);
   }
   CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, skip, s));                        // Z = S y
   CP_TRY(launch_apply_K(d, B.Gnm, B.Z, B.Kw, B.f, skip, s));                      // f = Kw - K Z
@@ -421,13 +411,13 @@ extern "C" int cp_dgn_core_build(const cp_shape* shape, const double* a, const d
   Layout L;
   make_layout(d, CP_CORE_F64, 0, &L);
   if (ws_bytes < L.total) return CP_ENOMEM;
-  Bufs B = carve(L, ws);
+  Bufs B = carve(L, ws, d.ncore);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (info) CP_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
-  CP_TRY(launch_gram(d, a, m, B.C, B.P, B.Gnm, B.Gall, nullptr, s));
-  CP_TRY(launch_mode_prep(d, B.C, B.Gnm, B.P, mu, Gt, B.U, B.LC, w, info, nullptr, s));
+  CP_TRY(launch_gram(d, a, m, B.gpart, B.C, B.P, nullptr, nullptr, nullptr, s));
+  CP_TRY(launch_mode_prep(d, B.C, B.P, mu, B.Gnm, Gt, B.U, B.LC, w, info, nullptr, s));
   CP_TRY(launch_core_w(d, B.Gnm, B.LC, B.U, B.Wp, nullptr, s));
-  CP_TRY(launch_core_fill<double>(d, B.LC, B.U, B.Wp, core, nullptr, s));
+  CP_TRY(launch_core_fill<double>(d, B.LC, B.U, B.Wp, core, 0, nullptr, s));
   return CP_OK;
 }
 
@@ -440,12 +430,12 @@ extern "C" int cp_dgn_solve(const cp_shape* shape, const double* a, const double
   Layout L;
   make_layout(d, CP_CORE_F64, 0, &L);
   if (ws_bytes < L.total) return CP_ENOMEM;
-  Bufs B = carve(L, ws);
+  Bufs B = carve(L, ws, d.ncore);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CP_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
   // S and K need the Gramians and the damped factors at (a, mu)
-  CP_TRY(launch_gram(d, a, nullptr, B.C, nullptr, B.Gnm, B.Gall, nullptr, s));
-  CP_TRY(launch_mode_prep(d, B.C, B.Gnm, B.P, mu, B.Gt, B.U, B.LC, nullptr, nullptr, nullptr, s));
+  CP_TRY(launch_gram(d, a, nullptr, B.gpart, B.C, nullptr, nullptr, nullptr, nullptr, s));
+  CP_TRY(launch_mode_prep(d, B.C, nullptr, mu, B.Gnm, B.Gt, B.U, B.LC, nullptr, nullptr, nullptr, s));
   CP_TRY(chol_factor<double>(core, d.ncore, info, nullptr, s));
   CP_CUDA(cudaMemcpyAsync(B.w, w, d.ncore * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CP_TRY(solve_core(d, B, core, nullptr, CP_CORE_F64, 0, nullptr, s));
@@ -470,7 +460,7 @@ extern "C" int cp_state_create(const cp_shape* shape, const cp_opts* opts, doubl
   st->a = a;
   st->ws = ws;
   st->L = L;
-  st->B = carve(L, ws);
+  st->B = carve(L, ws, d.ncore);
   *out = st;
   return CP_OK;
 }
@@ -508,7 +498,7 @@ extern "C" int cp_state_init(cp_state* st, const void* Y, void* stream) {
   int64_t g = (d.J + 255) / 256;
   if (g > 4 * kSMs) g = 4 * kSMs;
   k_sumsq<<<unsigned(g), 256, 0, s>>>(Y, d.y_dtype, d.J, B.scal + SC_YN2);
-  CP_TRY(launch_gram(d, st->a, nullptr, B.C, nullptr, B.Gnm, B.Gall, nullptr, s));
+  CP_TRY(launch_gram(d, st->a, nullptr, B.gpart, B.C, nullptr, B.Gnm, B.Gall, nullptr, s));
   k_init_status<<<1, 32, 0, s>>>(d, st->o, B.Gnm, B.scal, B.status, B.mu);
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
@@ -522,18 +512,19 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
   const double* mu = &B.status->mu;
   const int64_t nm = d.T * d.R;
   k_step_begin<<<unsigned((nm + 255) / 256 < 64 ? (nm + 255) / 256 : 64), 256, 0, s>>>(nm, B.mt, B.scal,
-                                                                                       B.info);
-  CP_TRY(launch_gram(d, st->a, B.m, B.C, B.P, B.Gnm, B.Gall, skip, s));
-  CP_TRY(launch_mode_prep(d, B.C, B.Gnm, B.P, mu, B.Gt, B.U, B.LC, B.w, B.info + IN_INFO, skip, s));
+                                                                                       B.info, B.status);
+  CP_TRY(launch_gram(d, st->a, B.m, B.gpart, B.C, B.P, nullptr, nullptr, skip, s));
+  CP_TRY(launch_mode_prep(d, B.C, B.P, mu, B.Gnm, B.Gt, B.U, B.LC, B.w, B.info + IN_INFO, skip, s));
   CP_TRY(launch_core_w(d, B.Gnm, B.LC, B.U, B.Wp, skip, s));
   if (st->o.core_mode == CP_CORE_F64) {
-    CP_TRY(launch_core_fill<double>(d, B.LC, B.U, B.Wp, B.core64, skip, s));
+    CP_TRY(launch_core_fill<double>(d, B.LC, B.U, B.Wp, B.core64, 0, skip, s));
     CP_TRY(chol_factor<double>(B.core64, d.ncore, B.info + IN_INFO, skip, s));
     CP_TRY(solve_core(d, B, B.core64, nullptr, CP_CORE_F64, 0, skip, s));
   } else {
-    CP_TRY(launch_core_fill<float>(d, B.LC, B.U, B.Wp, B.core32, skip, s));
-    CP_TRY(chol_factor<float>(B.core32, d.ncore, B.info + IN_INFO, skip, s));
-    CP_TRY(solve_core(d, B, nullptr, B.core32, CP_CORE_MIXED, st->o.refine_iters, skip, s));
+    CP_TRY(launch_core_fill<float>(d, B.LC, B.U, B.Wp, B.core32, 1, skip, s));
+    float* inv = nullptr;
+    CP_TRY(gj_invert<float>(B.core32, B.core32b, B.pinv, d.ncore, B.info + IN_INFO, skip, s, &inv));
+    CP_TRY(solve_core(d, B, nullptr, inv, CP_CORE_MIXED, st->o.refine_iters, skip, s));
   }
   const int64_t nupd = update_ctas(d);
   k_update<<<unsigned(nupd), kUpdRows * 32, 0, s>>>(d, st->a, B.m, B.Gnm, B.Gt, B.f, mu, B.delta, B.at,

@@ -53,5 +53,5 @@ def test_workspace_and_validation_host_only(lib):
     out = ctypes.c_size_t(0)
     assert cp._lib.cp_workspace_bytes(ctypes.byref(s), 7, 0, ctypes.byref(out)) == 1
     # null pointers are rejected on the host before any device work
-    assert cp._lib.cp_gram(ctypes.byref(s), None, None, None, None, None) == 1
+    assert cp._lib.cp_gram(ctypes.byref(s), None, None, None, None, None, 0, None) == 1
     assert cp._lib.cp_state_create(ctypes.byref(s), None, None, None, 0, None) == 1

@@ -44,8 +44,12 @@ def setup(cp, p, dtype=None):
     return shape, Y, a
 
 
+# ragged and degenerate shapes: N = 2..5, R = 1..32, I_1 = 1, I_n = 1, I_1 above
+# 256 / 512 / 768 rows (the tiled pass keeps 1, 2 or 3 rows per thread; above
+# that a generic pass takes over), I_2 smaller than a tile of fibres
 SHAPES = [((7, 9, 11), 3), ((20, 20, 20), 5), ((13, 6), 4), ((5, 4, 3, 6), 2), ((33, 17, 9), 1),
-          ((300, 5, 7), 6), ((4, 3, 2, 3, 2), 3), ((1, 8, 9), 2), ((9, 1, 7), 3), ((11, 12, 13), 32)]
+          ((300, 5, 7), 6), ((4, 3, 2, 3, 2), 3), ((1, 8, 9), 2), ((9, 1, 7), 3), ((11, 12, 13), 32),
+          ((600, 4, 5), 3), ((800, 3, 2), 2), ((20, 3, 40), 5), ((64, 2, 3, 50), 7), ((31, 29, 37), 17)]
 
 
 @pytest.mark.parametrize("dims,R", SHAPES)
