@@ -83,7 +83,7 @@ def run_profile(args):
                 cp.mttkrp_all(shape, Y, a, ws=ws)
         else:
             st = cp.State(shape, a, mu0=-1.0, mu_max=float("inf"), max_iter=10 ** 9,
-                          core_mode=cp.CP_CORE_MIXED, refine_iters=8)
+                          core_mode=cp.CP_CORE_MIXED if args.dtype != "f64" else cp.CP_CORE_F64, refine_iters=8)
             st.init(Y)
             for _ in range(args.warmup + args.steps):
                 st.step(Y)
