@@ -133,6 +133,22 @@ int cp_workspace_bytes(const cp_shape* shape, int core_mode, int what, size_t* b
 int cp_gram(const cp_shape* shape, const double* a, double* C, double* Gamma_nm,
             double* Gamma_all, void* ws, size_t ws_bytes, void* stream);
 
+/* cp_gram without a workspace argument, for callers that cannot allocate
+ * device memory (for example code inside a host framework that owns the
+ * whole device memory pool, or a plugin given only its inputs and outputs).
+ * It computes exactly what cp_gram computes; the paper has no counterpart of
+ * this call.  Its scratch (the per-row-block partial sums) is a fixed
+ * 2 MiB float64 array inside the library, present on every GPU that loads the
+ * library until the process exits; shapes whose partial sums exceed it
+ * (more than 2^18 doubles: ceil(I_n/8) summed over n, times R(R+1)/2 + R^2)
+ * return CP_ENOMEM.  The call allocates nothing.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it, so make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race; order them
+ * (one stream, or events). */
+int cp_gram_noalloc(const cp_shape* shape, const double* a, double* C, double* Gamma_nm,
+                    double* Gamma_all, void* stream);
+
 /* All-mode MTTKRP in one pass over Y (Algorithm 1 step 6, Sec. 4.6 Eq. mappingJ):
  *   m = [vec M_1; ...; vec M_N],  M_n = Y_(n) (A^(N) (.) ... A^(n+1) (.) A^(n-1) (.) ... A^(1)),
  * and, if resid2 != NULL, *resid2 = ||Y - Y_hat||_F^2 summed directly from the

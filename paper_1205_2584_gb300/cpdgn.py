@@ -67,6 +67,7 @@ _vp, _sz = ctypes.c_void_p, ctypes.c_size_t
 _sig = {
     "cp_workspace_bytes": [ctypes.POINTER(Shape), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_sz)],
     "cp_gram": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _sz, _vp],
+    "cp_gram_noalloc": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp],
     "cp_mttkrp_all": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _sz, _vp],
     "cp_fit": [ctypes.POINTER(Shape), _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _sz, _vp],
     "cp_dgn_core_build": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],

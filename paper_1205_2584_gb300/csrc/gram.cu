@@ -151,3 +151,55 @@ extern "C" int cp_gram(const cp_shape* shape, const double* a, double* C, double
   return launch_gram(d, a, nullptr, static_cast<double*>(ws), C, nullptr, Gamma_nm, Gamma_all, nullptr,
                      static_cast<cudaStream_t>(stream));
 }
+
+// ---------------------------------------------------------------------------
+// cp_gram_noalloc: cp_gram with its partial sums in a fixed device array.
+//
+// Some callers cannot allocate device memory: code running inside a host
+// framework that owns the whole device memory pool and forbids any further
+// allocation, or a plugin that is handed only its inputs and outputs.  This
+// entry point needs neither a workspace argument nor any allocation: the
+// partial sums of the row-block reduction live in the file-scope array
+// below, which every GPU that loads the library keeps until the process
+// exits.  All calls share it, so calls that overlap on the GPU (different
+// streams, no ordering between them) race and give wrong results; calls on
+// one stream, or otherwise ordered, are fine.  Nothing in it has to start at
+// zero: every call writes each partial it later reads.
+// ---------------------------------------------------------------------------
+namespace cpdgn {
+
+constexpr size_t kNoallocScratchDoubles = size_t(1) << 18;   // 2 MiB of float64 partials
+static __device__ __align__(256) double g_gram_scratch[kNoallocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+static double* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_gram_scratch on the current device, looked up once per
+// device (cudaGetSymbolAddress with that device current) and cached.
+static int noalloc_scratch(double** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CP_ECUDA;
+  double* p = __atomic_load_n(&g_scratch_ptr[dev], __ATOMIC_ACQUIRE);
+  if (!p) {
+    void* q = nullptr;
+    if (cudaGetSymbolAddress(&q, g_gram_scratch) != cudaSuccess || !q) return CP_ECUDA;
+    p = static_cast<double*>(q);
+    __atomic_store_n(&g_scratch_ptr[dev], p, __ATOMIC_RELEASE);
+  }
+  *out = p;
+  return CP_OK;
+}
+
+}  // namespace cpdgn
+
+extern "C" int cp_gram_noalloc(const cp_shape* shape, const double* a, double* C, double* Gamma_nm,
+                               double* Gamma_all, void* stream) {
+  Dims d;
+  CP_TRY(make_dims(shape, &d));
+  if (!a || !C) return CP_EINVAL;
+  if (gram_part_bytes(d) > kNoallocScratchDoubles * sizeof(double)) return CP_ENOMEM;
+  double* scratch = nullptr;
+  CP_TRY(noalloc_scratch(&scratch));
+  return launch_gram(d, a, nullptr, scratch, C, nullptr, Gamma_nm, Gamma_all, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
