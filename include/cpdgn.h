@@ -19,8 +19,9 @@
  *    length N R^2, mode-major, each R x R block column-major (Theorem 1:
  *    F_n is f[n R^2 : (n+1) R^2] reshaped R x R).
  *  - Every pointer is a device pointer unless its comment says "host".
- *    The caller owns every buffer; the library allocates nothing on any
- *    call below except cp_state_create (a small host-side handle).  All
+ *    The caller owns every buffer; the library allocates no device memory
+ *    on any call below; cp_state_create allocates a small host-side handle
+ *    (plus, in the mixed core mode, a CUDA stream and two events).  All
  *    device work is enqueued on `stream` and is asynchronous; device
  *    outputs are valid after the stream is synchronised.
  *  - Return value: CP_OK or a CP_E* code for errors detected on the host
@@ -195,7 +196,10 @@ int cp_dgn_solve(const cp_shape* shape, const double* a, const double* mu, doubl
  * ws: device workspace of cp_workspace_bytes(shape, opts->core_mode, 1) bytes,
  * which holds cp_status and every intermediate.  Both must stay valid until
  * cp_state_destroy.  *out receives the handle (host memory owned by the
- * library, freed by cp_state_destroy). */
+ * library, freed by cp_state_destroy).  In CP_CORE_MIXED the handle also owns
+ * one non-blocking CUDA stream and two events (created here, destroyed by
+ * cp_state_destroy): the core inversion forks its pivot chain onto that
+ * stream and joins it back, so steps stay ordered on the caller's stream. */
 int cp_state_create(const cp_shape* shape, const cp_opts* opts, double* a, void* ws,
                     size_t ws_bytes, cp_state** out);
 int cp_state_destroy(cp_state* st);

@@ -30,8 +30,11 @@ namespace cpdgn {
 constexpr int kRR = CP_MAX_R * CP_MAX_R;
 
 // In-place lower Cholesky of the R x R matrix G (column-major, ld R) by one
-// warp (lane = row).  Returns false on a non-positive or non-finite pivot.
-__device__ bool warp_chol(double* G, int R) {
+// warp (lane = row); rinv[k] receives 1 / L[k,k].  Float64 divides and square
+// roots are slow on this part (2 float64 lanes per clock per SM), so each step
+// takes one of each and the column is scaled by a multiply.  Returns false on
+// a non-positive or non-finite pivot.
+__device__ bool warp_chol(double* G, double* rinv, int R) {
   const int lane = threadIdx.x & 31;
   bool ok = true;
   for (int k = 0; k < R; ++k) {
@@ -39,10 +42,14 @@ __device__ bool warp_chol(double* G, int R) {
     const double piv = G[k + R * k];
     if (!(piv > 0.0) || !isfinite(piv)) ok = false;
     const double dk = sqrt(piv);
+    const double ik = 1.0 / dk;
     double lik = 0.0;
-    if (lane > k && lane < R) lik = G[lane + R * k] / dk;
+    if (lane > k && lane < R) lik = G[lane + R * k] * ik;
     __syncwarp();
-    if (lane == k) G[k + R * k] = dk;
+    if (lane == k) {
+      G[k + R * k] = dk;
+      rinv[k] = ik;
+    }
     if (lane > k && lane < R) G[lane + R * k] = lik;
     __syncwarp();
     if (lane > k && lane < R)
@@ -52,12 +59,12 @@ __device__ bool warp_chol(double* G, int R) {
   return ok;
 }
 
-// z <- L^{-1} z, one warp.
-__device__ void warp_fwd(const double* L, double* z, int R) {
+// z <- L^{-1} z, one warp; rinv = 1 / diag(L).
+__device__ void warp_fwd(const double* L, const double* rinv, double* z, int R) {
   const int lane = threadIdx.x & 31;
   for (int p = 0; p < R; ++p) {
     __syncwarp();
-    const double zp = z[p] / L[p + R * p];
+    const double zp = z[p] * rinv[p];
     __syncwarp();
     if (lane == p) z[p] = zp;
     if (lane > p && lane < R) z[lane] = fma(-L[lane + R * p], zp, z[lane]);
@@ -66,11 +73,11 @@ __device__ void warp_fwd(const double* L, double* z, int R) {
 }
 
 // z <- L^{-T} z, one warp.
-__device__ void warp_bwd(const double* L, double* z, int R) {
+__device__ void warp_bwd(const double* L, const double* rinv, double* z, int R) {
   const int lane = threadIdx.x & 31;
   for (int p = R - 1; p >= 0; --p) {
     __syncwarp();
-    const double zp = z[p] / L[p + R * p];
+    const double zp = z[p] * rinv[p];
     __syncwarp();
     if (lane == p) z[p] = zp;
     if (lane < p) z[lane] = fma(-L[p + R * lane], zp, z[lane]);
@@ -80,31 +87,46 @@ __device__ void warp_bwd(const double* L, double* z, int R) {
 
 constexpr int kPrepThreads = 128;
 
-// CTA (n, j): column j of Gt^(n), U_n, L_n = chol(C^(n)) and w_n.
+// CTA (n, j), j < R: column j of Gt^(n), U_n and w_n.
 //   Gt[:, j] = L_G^{-T} L_G^{-1} e_j;  U[:, j] = L_G^{-T} e_j
 //   w_n[:, j] = P^(n) Gt[:, j] - C^(n) (Gamma^(n) Gt[:, j])     (Appendix D)
 // CTA (n, 0) also writes Gamma^(n,m) for every m.
+// CTA N R + n: L_n = chol(C^(n)) (independent of mu).
 __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double* C, const double* P,
                                                             const double* mu, double* Gnm, double* Gt,
                                                             double* U, double* LC, double* w, int* info,
                                                             const int* skip) {
   if (skip && *skip) return;
-  __shared__ double G[kRR], Gam[kRR], Lc[kRR], Cn[kRR], Pn[kRR];
-  __shared__ double z[CP_MAX_R], u[CP_MAX_R], v[CP_MAX_R];
-  __shared__ int ok2[2];
+  __shared__ double G[kRR], Gam[kRR], Cn[kRR], Pn[kRR];
+  __shared__ double z[CP_MAX_R], u[CP_MAX_R], v[CP_MAX_R], rinv[CP_MAX_R];
+  __shared__ int okc;
   const int R = d.R, RR = d.RR, N = d.N;
-  const int n = blockIdx.x / R, j = blockIdx.x % R;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  if (int(blockIdx.x) >= N * R) {                 // Cholesky of C^(n)
+    const int n = blockIdx.x - N * R;
+    for (int e = tid; e < RR; e += kPrepThreads) G[e] = C[int64_t(n) * RR + e];
+    __syncthreads();
+    if (warp == 0) {
+      const bool ok = warp_chol(G, rinv, R);
+      if (lane == 0) okc = ok;
+    }
+    __syncthreads();
+    if (tid == 0 && info && !okc) atomicCAS(info, 0, n + 1);
+    for (int e = tid; e < RR; e += kPrepThreads) {
+      const int i = e % R, jj = e / R;
+      LC[int64_t(n) * RR + e] = (i >= jj) ? G[e] : 0.0;
+    }
+    return;
+  }
+  const int n = blockIdx.x / R, j = blockIdx.x % R;
   const double muv = *mu;
   for (int e = tid; e < RR; e += kPrepThreads) {
     double g = 1.0;
     for (int k = 0; k < N; ++k)
       if (k != n) g *= C[int64_t(k) * RR + e];
-    const double c = C[int64_t(n) * RR + e];
     Gam[e] = g;
     G[e] = g + ((e % R) == (e / R) ? muv : 0.0);
-    Cn[e] = c;
-    Lc[e] = c;
+    Cn[e] = C[int64_t(n) * RR + e];
     Pn[e] = P ? P[int64_t(n) * RR + e] : 0.0;
     if (j == 0 && Gnm) {
       for (int m = 0; m < N; ++m) {
@@ -117,23 +139,20 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
   }
   __syncthreads();
   if (warp == 0) {
-    const bool okG = warp_chol(G, R);
-    if (lane == 0) ok2[0] = okG;
-  } else if (warp == 1) {
-    const bool okC = warp_chol(Lc, R);
-    if (lane == 0) ok2[1] = okC;
+    const bool okG = warp_chol(G, rinv, R);
+    if (lane == 0) okc = okG;
   }
   __syncthreads();
-  if (tid == 0 && j == 0 && info && !(ok2[0] && ok2[1])) atomicCAS(info, 0, n + 1);
+  if (tid == 0 && j == 0 && info && !okc) atomicCAS(info, 0, n + 1);
   if (warp == 0) {
     if (lane < R) z[lane] = (lane == j) ? 1.0 : 0.0;
-    warp_fwd(G, z, R);
-    warp_bwd(G, z, R);   // z = Gt e_j
+    warp_fwd(G, rinv, z, R);
+    warp_bwd(G, rinv, z, R);   // z = Gt e_j
   } else if (warp == 1) {
     if (lane < R) u[lane] = (lane == j) ? 1.0 : 0.0;
-    warp_bwd(G, u, R);   // u = L_G^{-T} e_j
   }
   __syncthreads();
+  if (warp == 1) warp_bwd(G, rinv, u, R);   // u = L_G^{-T} e_j (overlaps the products below)
   if (tid < R) {
     double s = 0.0;
     for (int c = 0; c < R; ++c) s = fma(Gam[tid + R * c], z[c], s);
@@ -147,7 +166,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
     for (int c = 0; c < R; ++c) t = fma(Cn[tid + R * c], v[c], t);
     Gt[o] = z[tid];
     U[o] = u[tid];
-    LC[o] = (tid >= j) ? Lc[tid + R * j] : 0.0;
     if (w) w[o] = s - t;
   }
 }
@@ -155,7 +173,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
 int launch_mode_prep(const Dims& d, const double* C, const double* P, const double* mu, double* Gnm,
                      double* Gt, double* U, double* LC, double* w, int* info, const int* skip,
                      cudaStream_t s) {
-  k_mode_prep<<<d.N * d.R, kPrepThreads, 0, s>>>(d, C, P, mu, Gnm, Gt, U, LC, w, info, skip);
+  k_mode_prep<<<d.N * d.R + d.N, kPrepThreads, 0, s>>>(d, C, P, mu, Gnm, Gt, U, LC, w, info, skip);
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 

@@ -85,6 +85,7 @@ __global__ void k_gram_reduce(Dims d, const double* part, bool withP, double* C,
   for (int k = 0; k < n; ++k) c0 += (d.I[k] + kGramRows - 1) / kGramRows;
   const int64_t c1 = c0 + (d.I[n] + kGramRows - 1) / kGramRows;
   double s = 0.0;
+#pragma unroll 8
   for (int64_t c = c0; c < c1; ++c) s += part[c * E + e];
   if (e < nC) {
     int col = int((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);

@@ -518,6 +518,420 @@ __global__ void __launch_bounds__(kT2) k_mttkrp_tiled(Tiled p) {
 }
 
 // ---------------------------------------------------------------------------
+// k_mttkrp3: the production pass.  Per tile of TF fibres (double-buffered in
+// shared memory with cp.async), three register-tiled products that every
+// thread shares, each inner step fed by 16-byte shared-memory loads:
+//   B: M_1[i, r]  += sum_f y[i, f] kr_f[r]          4 rows x 4 r per thread,
+//                                                    accumulators live in
+//                                                    registers across tiles
+//   C: yh[i, f]    = sum_r A1[i, r] kr_f[r],  e2 += (y - yh)^2
+//                                                    4 rows x 4 fibres
+//   A: t_f[r]      = sum_i y[i, f] A1[i, r]          8 fibres x 4 r over
+//                                                    kSeg row segments
+// then t is summed over segments and M_n[i_n(f)] += t_f * loo_f(n), n >= 2:
+// mode 2 into a shared-memory partial (tile fibres have distinct i_2 when
+// TF <= I_2), modes >= 3 by one thread per (n, r) that sums the tile's fibres
+// per i_n run and adds the run to the float64 output.
+// ---------------------------------------------------------------------------
+constexpr int kT3 = 256;
+constexpr int kSeg3 = 16;
+
+struct P3 {
+  Dims d;
+  const void* Y;
+  const double* a;
+  double* m;
+  double* resid2;
+  const int* skip;
+  int64_t fib_per_cta;
+  int TF, ldy, Rp, ldi, nrb, npairB, FS;
+  int mn2_smem;           // 1: mode-2 partial in shared memory
+};
+
+template <typename TY>
+__device__ __forceinline__ void tile_copy3(const TY* Y, int64_t f0, int nf, int I1, int ldy, float* dst);
+template <>
+__device__ __forceinline__ void tile_copy3<float>(const float* Y, int64_t f0, int nf, int I1, int ldy,
+                                                  float* dst) {
+  const int tot = nf * I1;
+  const int64_t base = f0 * I1;
+  int f = 0, i = threadIdx.x;
+  while (i >= I1 && f < nf) { i -= I1; ++f; }
+  for (int e = threadIdx.x; e < tot; e += kT3) {
+    cp_async_elem<float>(dst + f * ldy + i, Y + base + e);
+    i += kT3;
+    while (i >= I1) { i -= I1; ++f; }
+  }
+}
+template <>
+__device__ __forceinline__ void tile_copy3<__nv_bfloat16>(const __nv_bfloat16* Y, int64_t f0, int nf, int I1,
+                                                          int ldy, float* dst) {
+  const int tot = nf * I1;
+  const int64_t base = f0 * I1;
+  int f = 0, i = threadIdx.x;
+  while (i >= I1 && f < nf) { i -= I1; ++f; }
+  for (int e = threadIdx.x; e < tot; e += kT3) {
+    dst[f * ldy + i] = __bfloat162float(Y[base + e]);
+    i += kT3;
+    while (i >= I1) { i -= I1; ++f; }
+  }
+}
+
+template <typename TY, int PB>
+__global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
+  if (p.skip && *p.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims& d = p.d;
+  const int R = d.R, N = d.N, Rp = p.Rp;
+  const int I1 = int(d.I[0]);
+  const int TF = p.TF, ldy = p.ldy, ldi = p.ldi;
+  const int tid = threadIdx.x;
+  const bool want_m = p.m != nullptr;
+
+  float* A1s = reinterpret_cast<float*>(smem_raw);             // ldi x Rp   [i][r]
+  float* A1t = A1s + size_t(ldi) * Rp;                          // Rp x ldi   [r][i]
+  float* krs = A1t + size_t(Rp) * ldi;                          // TF x Rp    [f][r]
+  float* krt = krs + size_t(TF) * Rp;                           // Rp x TF    [r][f]
+  float* ts = krt + size_t(Rp) * TF;                            // kSeg3 x TF x Rp
+  float* loos = ts + size_t(kSeg3) * TF * Rp;                   // (N-1) x TF x Rp
+  float* Mn2 = loos + size_t(N - 1) * TF * Rp;                  // I_2 x R (if mn2_smem)
+  const int64_t mn2 = p.mn2_smem ? d.I[1] * R : 0;
+  float* Yt0 = Mn2 + ((mn2 + 3) & ~int64_t(3));                 // 2 x TF x ldy
+  float* Yt1 = Yt0 + size_t(TF) * ldy;
+  int* fidx = reinterpret_cast<int*>(Yt1 + size_t(TF) * ldy);   // TF x CP_MAX_N
+  double* red = reinterpret_cast<double*>(
+      (reinterpret_cast<uintptr_t>(fidx + TF * CP_MAX_N) + 15) & ~uintptr_t(15));
+
+  const double* a = p.a;
+  for (int e = tid; e < ldi * Rp; e += kT3) {
+    const int i = e / Rp, r = e % Rp;
+    const float v = (i < I1 && r < R) ? float(a[i + int64_t(r) * I1]) : 0.f;
+    A1s[e] = v;
+    A1t[r * ldi + i] = v;
+  }
+  for (int64_t e = tid; e < mn2; e += kT3) Mn2[e] = 0.f;
+
+  const int64_t f_begin = int64_t(blockIdx.x) * p.fib_per_cta;
+  const int64_t f_end = (f_begin + p.fib_per_cta < d.nfib) ? f_begin + p.fib_per_cta : d.nfib;
+  const TY* Y = reinterpret_cast<const TY*>(p.Y);
+
+  // product B ownership: pair q = tid + k * kT3 (k < PB) -> (row block, r block),
+  // with FS threads splitting the fibres of one pair when pairs are few
+  const int nrbB = p.nrb, ncb = Rp / 4, FS = p.FS;
+  float accB[PB][4][4];
+#pragma unroll
+  for (int k = 0; k < PB; ++k)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) accB[k][u][v] = 0.f;
+  double e2_total = 0.0;
+
+  if (f_begin < f_end) {
+    const int nf0 = int((f_end - f_begin) < TF ? (f_end - f_begin) : TF);
+    tile_copy3<TY>(Y, f_begin, nf0, I1, ldy, Yt0);
+  }
+  cp_async_commit();
+  int buf = 0;
+  for (int64_t f0 = f_begin; f0 < f_end; f0 += TF) {
+    const int nf = int((f_end - f0) < TF ? (f_end - f0) : TF);
+    float* Yc = buf ? Yt1 : Yt0;
+    float* Yn = buf ? Yt0 : Yt1;
+    const int64_t f1 = f0 + TF;
+    if (f1 < f_end) tile_copy3<TY>(Y, f1, int((f_end - f1) < TF ? (f_end - f1) : TF), I1, ldy, Yn);
+    cp_async_commit();
+    for (int f = tid; f < TF; f += kT3) {
+      int64_t rem = f0 + (f < nf ? f : 0);
+#pragma unroll
+      for (int k = 1; k < CP_MAX_N; ++k)
+        if (k < N) {
+          fidx[f * CP_MAX_N + k] = int(rem % d.I[k]);
+          rem /= d.I[k];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < TF * Rp; e += kT3) {
+      const int f = e / Rp, r = e % Rp;
+      const bool ok = (f < nf) && (r < R);
+      float v[CP_MAX_N];
+#pragma unroll
+      for (int k = 1; k < CP_MAX_N; ++k)
+        if (k < N) v[k] = ok ? float(a[d.aoff[k] + fidx[f * CP_MAX_N + k] + int64_t(r) * d.I[k]]) : 0.f;
+      float kr = 1.f;
+#pragma unroll
+      for (int k = 1; k < CP_MAX_N; ++k)
+        if (k < N) kr *= v[k];
+      kr = ok ? kr : 0.f;
+      krs[f * Rp + r] = kr;
+      krt[r * TF + f] = kr;
+      if (want_m) {
+#pragma unroll
+        for (int n = 1; n < CP_MAX_N; ++n)
+          if (n < N) {
+            float lo = 1.f;
+#pragma unroll
+            for (int k = 1; k < CP_MAX_N; ++k)
+              if (k < N && k != n) lo *= v[k];
+            loos[(size_t(n - 1) * TF + f) * Rp + r] = ok ? lo : 0.f;
+          }
+      }
+    }
+    cp_async_wait<1>();
+    __syncthreads();
+
+    // ---- product B: M_1 += Y_tile KR_tile ----
+    if (want_m) {
+#pragma unroll
+      for (int k = 0; k < PB; ++k) {
+        const int q = (tid / FS) + k * (kT3 / FS);
+        const int fs = tid % FS;
+        if (q < p.npairB) {
+          const int rb = q % nrbB, cb = q / nrbB;
+          for (int f = fs; f < nf; f += FS) {
+            const float4 y4 = *reinterpret_cast<const float4*>(Yc + f * ldy + rb * 4);
+            const float4 k4 = *reinterpret_cast<const float4*>(krs + f * Rp + cb * 4);
+            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+            const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) accB[k][u][v] = fmaf(yv[u], kv[v], accB[k][u][v]);
+          }
+        }
+      }
+    }
+    // ---- product C: residual ----
+    {
+      const int nfb = TF / 4;
+      float e2 = 0.f;
+      for (int q = tid; q < nrbB * nfb; q += kT3) {
+        const int rb = q % nrbB, fb = q / nrbB;
+        float c[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) c[u][v] = 0.f;
+        for (int r = 0; r < Rp; ++r) {
+          const float4 a4 = *reinterpret_cast<const float4*>(A1t + r * ldi + rb * 4);
+          const float4 k4 = *reinterpret_cast<const float4*>(krt + r * TF + fb * 4);
+          const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+          const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) c[u][v] = fmaf(av[u], kv[v], c[u][v]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int f = fb * 4 + v;
+          if (f < nf) {
+            const float4 y4 = *reinterpret_cast<const float4*>(Yc + f * ldy + rb * 4);
+            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float e = (rb * 4 + u < I1) ? yv[u] - c[u][v] : 0.f;
+              e2 = fmaf(e, e, e2);
+            }
+          }
+        }
+      }
+      e2_total += double(e2);
+    }
+    // ---- product A: t partials ----
+    if (want_m) {
+      const int nfb8 = TF / 8, seg = (I1 + kSeg3 - 1) / kSeg3;
+      for (int task = tid; task < nfb8 * ncb * kSeg3; task += kT3) {
+        const int cb = task % ncb, fb = (task / ncb) % nfb8, sg = task / (ncb * nfb8);
+        const int ib = sg * seg, ie = (ib + seg < I1) ? ib + seg : I1;
+        float c[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) c[u][v] = 0.f;
+        const float* yb = Yc + fb * 8 * ldy;
+        for (int i = ib; i < ie; ++i) {
+          const float4 a4 = *reinterpret_cast<const float4*>(A1s + i * Rp + cb * 4);
+          const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float yv = yb[u * ldy + i];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) c[u][v] = fmaf(yv, av[v], c[u][v]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          *reinterpret_cast<float4*>(ts + (size_t(sg) * TF + fb * 8 + u) * Rp + cb * 4) =
+              make_float4(c[u][0], c[u][1], c[u][2], c[u][3]);
+      }
+    }
+    __syncthreads();
+    if (want_m) {
+      for (int e = tid; e < TF * Rp; e += kT3) {
+        float sum = ts[e];
+#pragma unroll
+        for (int sg = 1; sg < kSeg3; ++sg) sum += ts[size_t(sg) * TF * Rp + e];
+        ts[e] = sum;
+      }
+      __syncthreads();
+      // mode 2
+      if (p.mn2_smem) {
+        if (TF <= d.I[1]) {
+          for (int e = tid; e < nf * R; e += kT3) {
+            const int f = e / R, r = e % R;
+            Mn2[int64_t(fidx[f * CP_MAX_N + 1]) * R + r] += ts[f * Rp + r] * loos[f * Rp + r];
+          }
+        } else {
+          for (int e = tid; e < nf * R; e += kT3) {
+            const int f = e / R, r = e % R;
+            atomicAdd(&Mn2[int64_t(fidx[f * CP_MAX_N + 1]) * R + r], ts[f * Rp + r] * loos[f * Rp + r]);
+          }
+        }
+      }
+      // modes >= 3 (and mode 2 without the shared partial): per (n, r), runs of equal i_n
+      const int n_lo = p.mn2_smem ? 2 : 1;
+      for (int task = tid; task < (N - n_lo) * R; task += kT3) {
+        const int n = n_lo + task / R, r = task % R;
+        int cur = fidx[n];
+        float sacc = 0.f;
+        for (int f = 0; f < nf; ++f) {
+          const int in = fidx[f * CP_MAX_N + n];
+          if (in != cur) {
+            atomicAdd(&p.m[d.aoff[n] + cur + int64_t(r) * d.I[n]], double(sacc));
+            sacc = 0.f;
+            cur = in;
+          }
+          sacc = fmaf(ts[f * Rp + r], loos[(size_t(n - 1) * TF + f) * Rp + r], sacc);
+        }
+        atomicAdd(&p.m[d.aoff[n] + cur + int64_t(r) * d.I[n]], double(sacc));
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  cp_async_wait<0>();
+  if (want_m) {
+#pragma unroll
+    for (int k = 0; k < PB; ++k) {
+      const int q = (tid / FS) + k * (kT3 / FS);
+      if (q < p.npairB) {
+        const int rb = q % nrbB, cb = q / nrbB;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int i = rb * 4 + u, r = cb * 4 + v;
+            if (i < I1 && r < R) atomicAdd(&p.m[i + int64_t(r) * I1], double(accB[k][u][v]));
+          }
+      }
+    }
+    if (p.mn2_smem) {
+      const int I2 = int(d.I[1]);
+      for (int e = tid; e < I2 * R; e += kT3) {
+        const int i = e % I2, r = e / I2;
+        atomicAdd(&p.m[d.aoff[1] + i + int64_t(r) * I2], double(Mn2[int64_t(i) * R + r]));
+      }
+    }
+  }
+  if (p.resid2) {
+    const double sum = block_sum<kT3>(e2_total, red);
+    if (tid == 0) atomicAdd(p.resid2, sum);
+  }
+}
+
+static size_t smem3(const Dims& d, int TF, int ldy, int Rp, int ldi, int mn2_smem) {
+  size_t f = size_t(ldi) * Rp * 2 + size_t(TF) * Rp * 2 + size_t(kSeg3) * TF * Rp + size_t(d.N - 1) * TF * Rp;
+  if (mn2_smem) f += (size_t(d.I[1]) * d.R + 3) & ~size_t(3);
+  f += 2 * size_t(TF) * ldy;
+  return f * 4 + size_t(TF) * CP_MAX_N * 4 + 16 + kT3 * 8 + 16;
+}
+
+template <typename TY, int PB>
+static int launch3_t(const P3& p, int grid, size_t smem, cudaStream_t s) {
+  auto kern = k_mttkrp3<TY, PB>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    return CP_ECUDA;
+  kern<<<grid, kT3, smem, s>>>(p);
+  return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
+}
+
+// Returns CP_OK and launches, or CP_EINVAL when the shape does not fit this
+// kernel (the caller then uses the generic pass).
+int launch_mttkrp3(const Dims& d, const void* Y, const double* a, double* m, double* resid2, const int* skip,
+                   cudaStream_t s) {
+  if (d.y_dtype == CP_F64) return CP_EINVAL;
+  const int I1 = int(d.I[0]);
+  const int Rp = (d.R + 3) / 4 * 4;
+  const int nrb = (I1 + 3) / 4;
+  const int npairB = nrb * (Rp / 4);
+  int PB = (npairB + kT3 - 1) / kT3;
+  if (PB > 4) return CP_EINVAL;
+  if (PB == 3) PB = 4;
+  int FS = 1;
+  if (PB == 1) {
+    while (FS < 8 && npairB * FS * 2 <= kT3) FS *= 2;
+  }
+  const int ldi = nrb * 4;
+  int TF = int(16384 / (size_t(I1) * 4));
+  if (TF > 64) TF = 64;
+  TF &= ~7;
+  if (TF < 8) TF = 8;
+  // leading dimension: a multiple of 4 floats (16-byte rows), 4 mod 32 words
+  int ldy = (I1 + 3) / 4 * 4;
+  while (ldy % 32 != 4) ldy += 4;
+  const size_t max_smem = 200 * 1024;
+  int mn2_smem = 1;
+  size_t smem = smem3(d, TF, ldy, Rp, ldi, 1);
+  if (smem > max_smem || d.I[1] * d.R > 16384) {
+    mn2_smem = 0;
+    smem = smem3(d, TF, ldy, Rp, ldi, 0);
+  }
+  while (smem > max_smem && TF > 8) {
+    TF = (TF / 2) & ~7;
+    if (TF < 8) TF = 8;
+    smem = smem3(d, TF, ldy, Rp, ldi, mn2_smem);
+  }
+  if (smem > max_smem) return CP_EINVAL;
+  int per_sm = int((228 * 1024) / (smem + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 3) per_sm = 3;
+  const int64_t ntiles = (d.nfib + TF - 1) / TF;
+  int64_t grid = int64_t(kSMs) * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  const int64_t tiles_per = (ntiles + grid - 1) / grid;
+  P3 p;
+  p.d = d;
+  p.Y = Y;
+  p.a = a;
+  p.m = m;
+  p.resid2 = resid2;
+  p.skip = skip;
+  p.fib_per_cta = tiles_per * TF;
+  p.TF = TF;
+  p.ldy = ldy;
+  p.Rp = Rp;
+  p.ldi = ldi;
+  p.nrb = nrb;
+  p.npairB = npairB;
+  p.FS = FS;
+  p.mn2_smem = mn2_smem;
+  grid = (d.nfib + p.fib_per_cta - 1) / p.fib_per_cta;
+  if (d.y_dtype == CP_F32) {
+    switch (PB) {
+      case 1: return launch3_t<float, 1>(p, int(grid), smem, s);
+      case 2: return launch3_t<float, 2>(p, int(grid), smem, s);
+      default: return launch3_t<float, 4>(p, int(grid), smem, s);
+    }
+  }
+  switch (PB) {
+    case 1: return launch3_t<__nv_bfloat16, 1>(p, int(grid), smem, s);
+    case 2: return launch3_t<__nv_bfloat16, 2>(p, int(grid), smem, s);
+    default: return launch3_t<__nv_bfloat16, 4>(p, int(grid), smem, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static int rmax_for(int R) {
@@ -596,6 +1010,7 @@ static size_t tiled_smem(const Dims& d, int TF, int ldy, int Rp, size_t ta, size
 // Enqueue one pass (m and resid2 must already be zeroed).
 int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, double* resid2,
                   const int* skip, cudaStream_t s) {
+  if (launch_mttkrp3(d, Y, a, m, resid2, skip, s) == CP_OK) return CP_OK;
   const size_t ta = (d.y_dtype == CP_F64) ? sizeof(double) : sizeof(float);
   const size_t ty = (d.y_dtype == CP_F64) ? 8 : (d.y_dtype == CP_F32 ? 4 : 2);
   const int I1 = int(d.I[0]);

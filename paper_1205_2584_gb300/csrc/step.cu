@@ -47,7 +47,8 @@ int chol_factor(T* A, int64_t n, int* info, const int* skip, cudaStream_t s);
 template <typename T, typename TX>
 int chol_solve(const T* L, int64_t n, TX* x, TX* tmp, TX* y, const int* skip, cudaStream_t s);
 template <typename T>
-int gj_invert(T* A, T* B, T* pinv, int64_t n, int* info, const int* skip, cudaStream_t s, T** result);
+int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const int* skip, cudaStream_t s,
+              cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result);
 int launch_gemv_acc(const float* X, int64_t n, const double* r, double* y, const double* b2, const double* r2,
                     const double* r2prev, int* done, double tol2, const int* skip, cudaStream_t s);
 
@@ -205,6 +206,7 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
     for (int k = 0; k < n; ++k) c0 += (d.I[k] + kUpdRows - 1) / kUpdRows;
     const int64_t c1 = c0 + (d.I[n] + kUpdRows - 1) / kUpdRows;
     double s = 0.0;
+#pragma unroll 8
     for (int64_t c = c0; c < c1; ++c) s += part[c * (1 + R) + 1 + r];
     norms[tid] = s;
   }
@@ -377,6 +379,8 @@ struct cp_state {
   void* ws;
   Layout L;
   Bufs B;
+  cudaStream_t side = nullptr;           // second stream for the pivot chain of the core inversion
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_steps = 0;
@@ -443,6 +447,8 @@ extern "C" int cp_dgn_solve(const cp_shape* shape, const double* a, const double
   return CP_OK;
 }
 
+extern "C" int cp_state_destroy(cp_state* st);
+
 extern "C" int cp_state_create(const cp_shape* shape, const cp_opts* opts, double* a, void* ws,
                                size_t ws_bytes, cp_state** out) {
   if (!opts || !a || !ws || !out) return CP_EINVAL;
@@ -461,12 +467,25 @@ extern "C" int cp_state_create(const cp_shape* shape, const cp_opts* opts, doubl
   st->ws = ws;
   st->L = L;
   st->B = carve(L, ws, d.ncore);
+  if (opts->core_mode == CP_CORE_MIXED) {
+    if (cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cp_state_destroy(st);
+      return CP_ECUDA;
+    }
+  }
   *out = st;
   return CP_OK;
 }
 
 extern "C" int cp_state_destroy(cp_state* st) {
-  if (st) drop_graph(st);
+  if (st) {
+    drop_graph(st);
+    if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+    if (st->ev_join) cudaEventDestroy(st->ev_join);
+    if (st->side) cudaStreamDestroy(st->side);
+  }
   delete st;
   return CP_OK;
 }
@@ -523,7 +542,9 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
   } else {
     CP_TRY(launch_core_fill<float>(d, B.LC, B.U, B.Wp, B.core32, 1, skip, s));
     float* inv = nullptr;
-    CP_TRY(gj_invert<float>(B.core32, B.core32b, B.pinv, d.ncore, B.info + IN_INFO, skip, s, &inv));
+    // the core's first R^2 x R^2 diagonal block is the identity
+    CP_TRY(gj_invert<float>(B.core32, B.core32b, B.pinv, d.ncore, d.RR, B.info + IN_INFO, skip, s, st->side,
+                            st->ev_fork, st->ev_join, &inv));
     CP_TRY(solve_core(d, B, nullptr, inv, CP_CORE_MIXED, st->o.refine_iters, skip, s));
   }
   const int64_t nupd = update_ctas(d);
