@@ -21,7 +21,9 @@ constexpr int GJB = 64;           // panel / tile width
 constexpr int GJT = 256;          // threads per CTA: a 16 x 16 grid of 4 x 4 blocks
 constexpr int GJL = GJB + 1;      // padded leading dimension in shared memory
 
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// Reciprocal of a pivot.  The float32 inverse only preconditions the float64
+// refinement, so the fast intrinsic division (about 2 ulp) is accurate enough.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 template <typename T>
@@ -194,7 +196,9 @@ constexpr int PVT = 1024;
 
 template <typename T>
 __device__ void gj_invert_2x2(T (&x)[2][2], int kb, T (*prow)[GJB], T (*pcol)[GJB], int* bad) {
+  __shared__ T pv[GJB];                                          // pivots, checked at the end
   const int tid = threadIdx.x, bi = tid % 32, bj = tid / 32;   // rows 2 bi + u, cols 2 bj + v
+#pragma unroll 2
   for (int p = 0; p < kb; ++p) {
     const int par = p & 1;
     const int hp = p >> 1, lp = p & 1;
@@ -208,6 +212,7 @@ __device__ void gj_invert_2x2(T (&x)[2][2], int kb, T (*prow)[GJB], T (*pcol)[GJ
     }
     __syncthreads();
     const T piv = prow[par][p];
+    if (tid == 0) pv[p] = piv;
     const T dinv = recip(piv);
     const T c0 = pcol[par][2 * bi], c1 = pcol[par][2 * bi + 1];
     const T r0 = prow[par][2 * bj] * dinv, r1 = prow[par][2 * bj + 1] * dinv;
@@ -228,8 +233,10 @@ __device__ void gj_invert_2x2(T (&x)[2][2], int kb, T (*prow)[GJB], T (*pcol)[GJ
         x[1][0] = -c1 * dinv;
       }
     }
-    if (tid == 0 && !(piv > T(0) && isfinite(piv)) && *bad == 0) *bad = p + 1;
   }
+  // check the recorded pivots once, after the elimination
+  __syncthreads();
+  if (tid < kb && !(pv[tid] > T(0) && isfinite(pv[tid]))) atomicMin(bad, tid + 1);
   __syncthreads();
 }
 
@@ -252,10 +259,10 @@ template <typename T>
 __device__ void pivot_store(T (&x)[2][2], int64_t n, int kk, int kb, T* Pinv, T* D, int* info,
                             T (*prow)[GJB], T (*pcol)[GJB], int* bad) {
   const int bi = threadIdx.x % 32, bj = threadIdx.x / 32;
-  if (threadIdx.x == 0) *bad = 0;
+  if (threadIdx.x == 0) *bad = GJB + 1;
   __syncthreads();
   gj_invert_2x2<T>(x, kb, prow, pcol, bad);
-  if (threadIdx.x == 0 && *bad && info) atomicCAS(info, 0, kk * GJB + *bad);
+  if (threadIdx.x == 0 && *bad <= GJB && info) atomicCAS(info, 0, kk * GJB + *bad);
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
