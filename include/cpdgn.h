@@ -241,6 +241,47 @@ cp_status* cp_state_status(cp_state* st);
  * Returns NULL for an unknown id. */
 double* cp_state_buffer(cp_state* st, int id);
 
+/* ---- batched form: many small decompositions in one persistent launch ---- */
+
+/* One problem of a batch.  Limits: 2 <= N <= 4, 1 <= R <= 16, I_1 <= 256,
+ * sum_{n>=2} I_n R <= 12288, N R^2 <= 1024. */
+typedef struct cp_batch_problem {
+  int32_t N;
+  int32_t R;
+  int64_t I[4];
+  int64_t y_off;     /* element offset of its float32 tensor (first index fastest)
+                        in the packed tensor buffer */
+  int64_t a_off;     /* float64 offset of its parameter vector a in the packed
+                        factor buffer (same layout as the single-problem calls) */
+  int64_t ws_off;    /* byte offset of its workspace; set by cp_batch_layout */
+  double mu0;        /* > 0: initial damping; otherwise opts->tau * max diag Gamma^(n) */
+} cp_batch_problem;
+
+/* CP_OK if the problem fits the batched kernel's limits (host-only). */
+int cp_batch_check(const cp_batch_problem* p);
+
+/* Host-only: assign every problem's ws_off and return the total workspace
+ * bytes (*ws_bytes) for cp_batch_run.  CP_EINVAL if a problem is out of range. */
+int cp_batch_layout(cp_batch_problem* probs, int count, size_t* ws_bytes);
+
+/* Run the batch: one persistent launch of `ctas` CTAs (<= 0: one per SM) that
+ * take problems from a device work queue; each CTA runs a taken problem's
+ * Levenberg-Marquardt trials (Algorithm 1 with the Sec. 4.6 control, the same
+ * algebra as cp_dgn_step) until its stop rule fires or `trials` trials have
+ * run in this launch, then takes the next problem.  probs_dev: device copy of
+ * the laid-out problems; Y: packed float32 tensors; a: packed float64 factors,
+ * updated in place; status: `count` cp_status, zero-filled by the caller
+ * before the first launch and carried across launches; ws: workspace of
+ * cp_batch_layout's size.  A later launch continues every problem that has not
+ * stopped.  The first 256 bytes of ws are the queue counter (reset here).
+ * tile: fibres per tile of the in-CTA pass over a tensor (8, 16 or 32; 0 =
+ * 16), a tuning knob that does not change results beyond rounding.  order
+ * (device, may be NULL): a permutation of 0..count-1 giving the queue order
+ * (e.g. most expensive first); results are always indexed by problem. */
+int cp_batch_run(const cp_batch_problem* probs_dev, int count, const float* Y, double* a, void* ws,
+                 cp_status* status, const cp_opts* opts, int trials, int ctas, int tile,
+                 const int* order, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,8 @@ _sig = {
     "cp_state_capture": [_vp, _vp, ctypes.c_int, _vp],
     "cp_state_launch": [_vp, _vp],
     "cp_state_graph_kernels": [_vp],
+    "cp_batch_run": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                     ctypes.c_int, _vp, _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -90,7 +92,19 @@ _lib.cp_state_status.restype = _vp
 _lib.cp_state_buffer.argtypes = [_vp, ctypes.c_int]
 _lib.cp_state_buffer.restype = _vp
 
-EXPORTED = list(_sig) + ["cp_state_status", "cp_state_buffer"]
+
+class BatchProblem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("R", ctypes.c_int32), ("I", ctypes.c_int64 * 4),
+                ("y_off", ctypes.c_int64), ("a_off", ctypes.c_int64), ("ws_off", ctypes.c_int64),
+                ("mu0", ctypes.c_double)]
+
+
+_lib.cp_batch_check.argtypes = [ctypes.POINTER(BatchProblem)]
+_lib.cp_batch_check.restype = ctypes.c_int
+_lib.cp_batch_layout.argtypes = [ctypes.POINTER(BatchProblem), ctypes.c_int, ctypes.POINTER(_sz)]
+_lib.cp_batch_layout.restype = ctypes.c_int
+
+EXPORTED = list(_sig) + ["cp_state_status", "cp_state_buffer", "cp_batch_check", "cp_batch_layout"]
 
 
 def _check(rc: int, what: str):
@@ -281,3 +295,101 @@ class State:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """Many small decompositions (float32 tensors) run by one persistent launch.
+
+    problems: list of (Y numpy array float32-representable, factors list, mu0).
+    Packs tensors, factors and workspace on the device; status stays there.
+    """
+
+    def __init__(self, problems, *, tol=0.0, mu_max=1e30, max_iter=1000, normalize=True, tau=1e-3,
+                 refine_iters=4, device="cuda"):
+        import numpy as np
+        count = len(problems)
+        arr = (BatchProblem * max(count, 1))()
+        ys, afs = [], []
+        yoff = aoff = 0
+        self.meta = []
+        for i, (Y, factors, mu0) in enumerate(problems):
+            dims = Y.shape
+            R = factors[0].shape[1]
+            p = arr[i]
+            p.N = len(dims)
+            p.R = R
+            for k in range(4):
+                p.I[k] = int(dims[k]) if k < len(dims) else 1
+            p.y_off = yoff
+            p.a_off = aoff
+            p.mu0 = float(mu0) if mu0 else -1.0
+            ys.append(np.asarray(Y, dtype=np.float32).ravel(order="F"))
+            afs.append(np.concatenate([np.asarray(f, dtype=np.float64).ravel(order="F") for f in factors]))
+            self.meta.append((tuple(int(d) for d in dims), R, aoff))
+            yoff += ys[-1].size
+            aoff += afs[-1].size
+            _check(_lib.cp_batch_check(ctypes.byref(p)), f"cp_batch_check(problem {i})")
+        nbytes = _sz(0)
+        _check(_lib.cp_batch_layout(arr, count, ctypes.byref(nbytes)), "cp_batch_layout")
+        self.count = count
+        self.Y = torch.from_numpy(np.concatenate(ys) if ys else np.zeros(1, np.float32)).to(device)
+        self.a = torch.from_numpy(np.concatenate(afs) if afs else np.zeros(1)).to(device)
+        self.a0 = self.a.clone()
+        self.ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=device)
+        raw = bytes(memoryview(arr)[: ctypes.sizeof(BatchProblem) * max(count, 1)])
+        self.probs = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+        self.status = torch.zeros(max(count, 1) * 128, dtype=torch.uint8, device=device)
+        self.opts = Opts(mu0=-1.0, tau=tau, tol=tol, mu_max=mu_max, max_iter=max_iter,
+                         normalize=1 if normalize else 0, core_mode=CP_CORE_MIXED, refine_iters=refine_iters)
+
+    def run(self, trials: int = 1 << 30, ctas: int = 0, tile: int = 0, order=None, stream=None):
+        """One persistent launch.  tile / order: tuning knobs (see cp_batch_run);
+        `order` may be a device int32 tensor, or "cost" for most-expensive-first."""
+        if isinstance(order, str) and order == "cost":
+            order = self.cost_order()
+        _check(_lib.cp_batch_run(_ptr(self.probs), self.count, _ptr(self.Y), _ptr(self.a), _ptr(self.ws),
+                                 _ptr(self.status), ctypes.byref(self.opts), int(trials), int(ctas), int(tile),
+                                 _ptr(order), _stream(stream)), "cp_batch_run")
+
+    def cost_order(self):
+        """Queue order with the most expensive problems first (longest-processing-
+        time-first list scheduling); cost ~ (N R^2)^3 / 3 + 3 R prod(I)."""
+        import numpy as np
+        if getattr(self, "_cost_order", None) is None:
+            cost = []
+            for dims, R, _ in self.meta:
+                n = len(dims) * R * R
+                cost.append(n ** 3 / 3.0 + 3.0 * R * float(np.prod(dims)))
+            idx = np.argsort(-np.asarray(cost), kind="stable").astype(np.int32)
+            self._cost_order = torch.from_numpy(idx).to(self.Y.device)
+        return self._cost_order
+
+    def reset(self):
+        """Back to the starting factors and a zeroed status (queue order kept)."""
+        self.a.copy_(self.a0)
+        self.status.zero_()
+
+    def run_tuned(self, trials: int = 1 << 30, stream=None, tune_trials: int = 2):
+        """Tune (or reuse the cached tuning for these shapes), then run."""
+        from . import autotune
+        cfg = autotune.tune_batch(self, trials=tune_trials, stream=stream)
+        self.run(trials=trials, tile=cfg["tile"], order=None if cfg["order"] == "given" else "cost",
+                 stream=stream)
+        return cfg
+
+    def statuses(self):
+        raw = self.status.cpu().numpy().tobytes()
+        out = []
+        for i in range(self.count):
+            d = Status.from_buffer_copy(raw[128 * i:128 * (i + 1)]).as_dict()
+            d["stop_reason"] = STOP.get(d["stop"], d["stop"])
+            out.append(d)
+        return out
+
+    def factors(self, i: int):
+        dims, R, aoff = self.meta[i]
+        return split_factors(self.a[aoff:aoff + R * sum(dims)].cpu(), dims, R)
