@@ -355,6 +355,17 @@ class Batch:
                                  _ptr(self.status), ctypes.byref(self.opts), int(trials), int(ctas), int(tile),
                                  _ptr(order), _stream(stream)), "cp_batch_run")
 
+    def capture(self, trials: int = 1 << 30, tile: int = 0, order=None):
+        """Capture one persistent launch (queue reset + kernel) in a CUDA graph;
+        returns the torch.cuda.CUDAGraph (replay() runs it on the current stream)."""
+        self.run(trials=1, tile=tile, order=order)      # sets the kernel's shared-memory attribute
+        torch.cuda.synchronize()
+        self.reset()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(trials=trials, tile=tile, order=order)
+        return g
+
     def cost_order(self):
         """Queue order with the most expensive problems first (longest-processing-
         time-first list scheduling); cost ~ (N R^2)^3 / 3 + 3 R prod(I)."""

@@ -198,11 +198,13 @@ def state_bytes(dims: Sequence[int], R: int) -> int:
     return 4 * int(np.prod(dims)) + 8 * R * int(sum(dims)) + cp.workspace_bytes(shape, cp.CP_CORE_MIXED, True)
 
 
-def synth_on_device(req: Request, device):
+def synth_on_device(req: Request, device, dtype=None):
     """Seeded request tensor and initial factors built on the device (torch
     Philox generator), standing in for a client's upload.  Returns (y, a):
-    y = float32 vec(Y) (first index fastest), a = float64 packed factors."""
+    y = vec(Y) (first index fastest) in `dtype` (float32 by default),
+    a = float64 packed factors."""
     import torch
+    dtype = torch.float32 if dtype is None else dtype
     g = torch.Generator(device=device).manual_seed(int(req.seed))
     facs = []
     for n, I in enumerate(req.dims):
@@ -216,7 +218,7 @@ def synth_on_device(req: Request, device):
     if req.snr_db is not None:
         sigma = 10.0 ** (-req.snr_db / 20.0) * torch.linalg.vector_norm(Y) / math.sqrt(Y.numel())
         Y = Y + sigma * torch.randn(Y.shape, generator=g, device=device, dtype=torch.float64)
-    y = Y.permute(*reversed(range(Y.dim()))).contiguous().reshape(-1).to(torch.float32)
+    y = Y.permute(*reversed(range(Y.dim()))).contiguous().reshape(-1).to(dtype)
     a = torch.cat([torch.randn(I, req.R, generator=g, device=device, dtype=torch.float64).t().reshape(-1)
                    for I in req.dims])
     return y, a
