@@ -63,7 +63,7 @@ def parse():
                    help="profiling driver: run only this part (no JSON line)")
     p.add_argument("--dims", default="", help="tensor dims for --profile, e.g. 400,400,400")
     p.add_argument("--rank", type=int, default=R)
-    p.add_argument("--dtype", default="f32", choices=["f64", "f32", "bf16"])
+    p.add_argument("--dtype", default="f32", choices=["f64", "f32", "bf16", "bf16x2"])
     return p.parse_args()
 
 
@@ -78,7 +78,8 @@ def run_profile(args):
     J = 1
     for d in dims:
         J *= d
-    Y = torch.randn(J, generator=g, device="cuda", dtype=torch.float32).to(cp.TORCH_DTYPE[shape.y_dtype])
+    Y = torch.randn(J, generator=g, device="cuda", dtype=torch.float32)
+    Y = cp.tensor_split(Y) if args.dtype == "bf16x2" else Y.to(cp.TORCH_DTYPE[shape.y_dtype])
     a = torch.randn(args.rank * sum(dims), generator=g, device="cuda", dtype=torch.float64)
     with torch.cuda.stream(torch.cuda.Stream()):
         if args.profile == "mttkrp":

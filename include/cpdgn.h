@@ -8,7 +8,8 @@
  * --------------------------------
  *  - Tensor Y (I_1 x ... x I_N) is dense with the first index fastest
  *    (column-major vec, Sec. 2 and Appendix A).  Its element type is
- *    cp_shape.y_dtype: float64, float32 or bfloat16.
+ *    cp_shape.y_dtype: float64, float32, bfloat16, or a pair of bfloat16
+ *    planes (CP_BF16X2, see below).
  *  - Factors are passed as ONE float64 device buffer `a` holding the paper's
  *    parameter vector a = [vec A^(1); ...; vec A^(N)] (Eq. vecV): A^(n) is
  *    I_n x R column-major at offset R * (I_1 + ... + I_{n-1}).  Buffers named
@@ -45,8 +46,16 @@ extern "C" {
 #define CP_MAX_N 8
 #define CP_MAX_R 32
 
-/* element type of the tensor */
-enum cp_dtype { CP_F64 = 0, CP_F32 = 1, CP_BF16 = 2 };
+/* element type of the tensor.
+ * CP_BF16X2: the tensor is stored as two bfloat16 planes of J elements each,
+ * back to back in one buffer (hi plane first, then lo plane, both in the
+ * column-major vec order); entry j has the value hi[j] + lo[j], 16 significant
+ * bits.  cp_tensor_split() writes this form from a float32 tensor (hi = the
+ * float32 value rounded to bfloat16, lo = the remainder rounded to bfloat16).
+ * The planes are the direct operands of the tensor-core pass, so this form is
+ * accepted only where that pass applies: N = 3, I_1 a multiple of 8 (the
+ * buffer must be 16-byte aligned); other shapes return CP_EINVAL. */
+enum cp_dtype { CP_F64 = 0, CP_F32 = 1, CP_BF16 = 2, CP_BF16X2 = 3 };
 
 /* status codes */
 enum cp_code {
@@ -74,8 +83,10 @@ typedef struct cp_shape {
   int32_t R;               /* rank, 1..CP_MAX_R */
   int64_t I[CP_MAX_N];     /* I_1..I_N; entries beyond N ignored */
   int32_t y_dtype;         /* enum cp_dtype of Y; float32 and bfloat16 tensors
-                              are contracted with float32 arithmetic, float64
-                              tensors with float64 arithmetic */
+                              are contracted with float32 arithmetic (on the
+                              tensor cores, with operands split into bfloat16
+                              pieces, where the shape allows), float64 tensors
+                              with float64 arithmetic */
   int32_t reserved;
 } cp_shape;
 
@@ -163,6 +174,16 @@ int cp_mttkrp_all(const cp_shape* shape, const void* Y, const double* a, double*
  * rel_err may be NULL).  Sec. 6.1 (epsilon). */
 int cp_fit(const cp_shape* shape, const void* Y, const double* a, double y_norm2,
            double* resid2, double* rel_err, void* ws, size_t ws_bytes, void* stream);
+
+/* Float32 tensor -> the CP_BF16X2 form (see enum cp_dtype): out[j] = hi, the
+ * float32 value rounded to bfloat16 (nearest even), out[J + j] = lo, the
+ * remainder y - hi rounded to bfloat16.  Y: J float32 values on the device;
+ * out: 2 J bfloat16 (4 J bytes) on the device, 16-byte aligned, not
+ * overlapping Y.  Enqueued on `stream`; the layout is the tensor's own, so
+ * any shape works.  Not a step of the paper's method: it prepares the tensor
+ * once for the tensor-core pass, which reads the two planes directly.
+ * CP_EINVAL for null pointers, J < 1 or an unaligned out. */
+int cp_tensor_split(const float* Y, int64_t J, void* out, void* stream);
 
 /* Core system of one damped step at factors `a` with MTTKRP `m` and damping
  * *mu (device scalar), Theorems 1 and 3 in symmetric positive definite form:

@@ -23,13 +23,14 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 CP_MAX_N = 8
 CP_MAX_R = 32
-CP_F64, CP_F32, CP_BF16 = 0, 1, 2
+CP_F64, CP_F32, CP_BF16, CP_BF16X2 = 0, 1, 2, 3
 CP_CORE_F64, CP_CORE_MIXED = 0, 1
 CODES = {0: "CP_OK", 1: "CP_EINVAL", 2: "CP_ENOTSPD", 3: "CP_ENONFINITE", 4: "CP_ETIMEOUT",
          5: "CP_ENOMEM", 6: "CP_ECUDA"}
 STOP = {0: "running", 1: "tol", 2: "mu_max", 3: "max_iter", 4: "error"}
-DTYPES = {"f64": CP_F64, "f32": CP_F32, "bf16": CP_BF16}
-TORCH_DTYPE = {CP_F64: torch.float64, CP_F32: torch.float32, CP_BF16: torch.bfloat16}
+DTYPES = {"f64": CP_F64, "f32": CP_F32, "bf16": CP_BF16, "bf16x2": CP_BF16X2}
+# storage dtype of Y; the CP_BF16X2 form holds 2 J bfloat16 values (hi plane, lo plane)
+TORCH_DTYPE = {CP_F64: torch.float64, CP_F32: torch.float32, CP_BF16: torch.bfloat16, CP_BF16X2: torch.bfloat16}
 
 
 class CPError(RuntimeError):
@@ -82,6 +83,7 @@ _sig = {
     "cp_state_graph_kernels": [_vp],
     "cp_batch_run": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                      ctypes.c_int, _vp, _vp],
+    "cp_tensor_split": [_vp, ctypes.c_int64, _vp, _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -159,10 +161,24 @@ def split_factors(a: torch.Tensor, dims: Sequence[int], R: int):
 
 
 def tensor_to_device(Y, y_dtype: str, device="cuda") -> torch.Tensor:
-    """Column-major (first index fastest) device copy of a numpy tensor."""
+    """Column-major (first index fastest) device copy of a numpy tensor; for
+    "bf16x2" the float32 values are split on the device (cp_tensor_split)."""
     import numpy as np
     flat = np.asarray(Y, dtype=np.float64).ravel(order="F")
+    if y_dtype == "bf16x2":
+        return tensor_split(torch.from_numpy(flat).to(torch.float32).to(device))
     return torch.from_numpy(flat).to(TORCH_DTYPE[DTYPES[y_dtype]]).to(device)
+
+
+def tensor_split(y32: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """float32 device tensor (vec order) -> the two-plane bfloat16 form
+    [hi plane | lo plane] consumed by CP_BF16X2 shapes."""
+    assert y32.dtype == torch.float32 and y32.is_cuda and y32.is_contiguous()
+    J = y32.numel()
+    if out is None:
+        out = torch.empty(2 * J, dtype=torch.bfloat16, device=y32.device)
+    _check(_lib.cp_tensor_split(_ptr(y32), J, _ptr(out), _stream(stream)), "cp_tensor_split")
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -29,7 +29,10 @@ struct Dims {
 inline int make_dims(const cp_shape* s, Dims* d) {
   if (!s || !d) return CP_EINVAL;
   if (s->N < 2 || s->N > CP_MAX_N || s->R < 1 || s->R > CP_MAX_R) return CP_EINVAL;
-  if (s->y_dtype != CP_F64 && s->y_dtype != CP_F32 && s->y_dtype != CP_BF16) return CP_EINVAL;
+  if (s->y_dtype != CP_F64 && s->y_dtype != CP_F32 && s->y_dtype != CP_BF16 && s->y_dtype != CP_BF16X2)
+    return CP_EINVAL;
+  // the two-plane form exists only for the tensor-core pass (3-way, I_1 % 8 == 0)
+  if (s->y_dtype == CP_BF16X2 && (s->N != 3 || s->I[0] % 8 != 0)) return CP_EINVAL;
   d->N = s->N;
   d->R = s->R;
   d->RR = s->R * s->R;

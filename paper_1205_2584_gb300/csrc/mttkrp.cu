@@ -1008,8 +1008,12 @@ static size_t tiled_smem(const Dims& d, int TF, int ldy, int Rp, size_t ta, size
 }
 
 // Enqueue one pass (m and resid2 must already be zeroed).
+int launch_mttkrp_tc(const Dims& d, const void* Y, const double* a, double* m, double* resid2, const int* skip,
+                     cudaStream_t s);
+
 int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, double* resid2,
                   const int* skip, cudaStream_t s) {
+  if (launch_mttkrp_tc(d, Y, a, m, resid2, skip, s) == CP_OK) return CP_OK;
   if (launch_mttkrp3(d, Y, a, m, resid2, skip, s) == CP_OK) return CP_OK;
   const size_t ta = (d.y_dtype == CP_F64) ? sizeof(double) : sizeof(float);
   const size_t ty = (d.y_dtype == CP_F64) ? 8 : (d.y_dtype == CP_F32 ? 4 : 2);

@@ -294,6 +294,9 @@ __global__ void k_sumsq(const void* Y, int dtype, int64_t J, double* out) {
     double v;
     if (dtype == CP_F64) v = static_cast<const double*>(Y)[i];
     else if (dtype == CP_F32) v = static_cast<const float*>(Y)[i];
+    else if (dtype == CP_BF16X2)
+      v = double(__bfloat162float(static_cast<const __nv_bfloat16*>(Y)[i])) +
+          double(__bfloat162float(static_cast<const __nv_bfloat16*>(Y)[J + i]));
     else v = __bfloat162float(static_cast<const __nv_bfloat16*>(Y)[i]);
     s = fma(v, v, s);
   }

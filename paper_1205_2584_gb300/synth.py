@@ -90,15 +90,20 @@ def add_noise(rng, Y: np.ndarray, snr_db: Optional[float]) -> np.ndarray:
 
 def cast_like(Y: np.ndarray, dtype: str) -> np.ndarray:
     """Round Y to the storage dtype and return the float64 values that the
-    stored tensor represents ("f64", "f32" or "bf16", round to nearest even)."""
+    stored tensor represents ("f64", "f32", "bf16", round to nearest even, or
+    "bf16x2": the float32 value as hi + lo, hi = bf16(y), lo = bf16(y - hi))."""
     if dtype == "f64":
         return np.asarray(Y, dtype=np.float64)
     if dtype == "f32":
         return np.asarray(Y, dtype=np.float32).astype(np.float64)
-    if dtype == "bf16":
+    if dtype in ("bf16", "bf16x2"):
         import torch
         t = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float32))
-        return t.to(torch.bfloat16).to(torch.float64).numpy()
+        hi = t.to(torch.bfloat16)
+        if dtype == "bf16":
+            return hi.to(torch.float64).numpy()
+        lo = (t - hi.to(torch.float32)).to(torch.bfloat16)
+        return (hi.to(torch.float64) + lo.to(torch.float64)).numpy()
     raise ValueError(dtype)
 
 

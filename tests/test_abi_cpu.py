@@ -50,6 +50,16 @@ def test_workspace_and_validation_host_only(lib):
                 cp.make_shape((5, 6), 33, "f64"), cp.make_shape((5, 0, 3), 2, "f64")]:
         with pytest.raises(cp.CPError):
             cp.workspace_bytes(bad)
+    # the two-plane bfloat16 form exists only for 3-way tensors with I_1 % 8 == 0
+    assert cp.workspace_bytes(cp.make_shape((64, 30, 7), 5, "bf16x2")) > 0
+    for bad in [cp.make_shape((60, 30, 7), 5, "bf16x2"), cp.make_shape((8, 8, 8, 8), 2, "bf16x2")]:
+        with pytest.raises(cp.CPError):
+            cp.workspace_bytes(bad)
+    bad_dtype = cp.make_shape((8, 8, 8), 2, "f32")
+    bad_dtype.y_dtype = 4
+    with pytest.raises(cp.CPError):
+        cp.workspace_bytes(bad_dtype)
+    assert cp._lib.cp_tensor_split(None, 8, None, None) == 1
     out = ctypes.c_size_t(0)
     assert cp._lib.cp_workspace_bytes(ctypes.byref(s), 7, 0, ctypes.byref(out)) == 1
     # null pointers are rejected on the host before any device work
