@@ -246,10 +246,13 @@ def _run_ours(args, rank, world, local):
 
     seed = args.seed + rank
     peaks, peak_src = measured_peaks()
-    prob32 = synth.config2(seed, DIMS, dtype="f32")
-    shape32 = cp.make_shape(DIMS, R, "f32")
+    # the tensor is stored as two bfloat16 planes (hi + lo, 16 significant
+    # bits) that the tensor-core pass reads directly; the oracle and the
+    # float64 form see the same values
+    prob = synth.config2(seed, DIMS, dtype="bf16x2")
+    shape2 = cp.make_shape(DIMS, R, "bf16x2")
     stream = torch.cuda.current_stream()
-    Y32 = cp.tensor_to_device(prob32.Y, "f32")
+    Y2 = cp.tensor_to_device(prob.Y, "bf16x2")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def new_state(shape, mode, a0, tol=0.0, max_iter=10 ** 9, mu_max=float("inf")):
@@ -275,11 +278,31 @@ def _run_ours(args, rank, world, local):
         barrier(world)
         return sum(a.elapsed_time(b) for a, b in ev), nk
 
-    # --- timed region: mixed form on the float32 tensor ---
-    st, a = new_state(shape32, cp.CP_CORE_MIXED, prob32.init)
-    st.init(Y32)
+    def time_pass(shape, Y, a_in, reps=20):
+        """cp_mttkrp_all (MTTKRP + direct residual, one pass) timed alone, L2 flushed."""
+        ws = cp.alloc_workspace(shape)
+        m = torch.empty_like(a_in)
+        r2 = torch.empty(1, dtype=torch.float64, device="cuda")
+        call = lambda: cp._lib.cp_mttkrp_all(cp.ctypes.byref(shape), cp._ptr(Y), cp._ptr(a_in), cp._ptr(m),
+                                             cp._ptr(r2), cp._ptr(ws), ws.numel(), cp._stream())
+        for _ in range(3):
+            call()
+        evs = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            call()
+            e1.record()
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    # --- timed region: mixed form (tensor-core pass, float32 core factor) ---
+    st, a = new_state(shape2, cp.CP_CORE_MIXED, prob.init)
+    st.init(Y2)
     with ClockSampler(local) as clk:
-        t_ms, nk = timed_steps(st, Y32, args.steps, args.warmup)
+        t_ms, nk = timed_steps(st, Y2, args.steps, args.warmup)
     status = st.status()
     t_ms = allmax(t_ms, world)
     ms_per_step = t_ms / args.steps
@@ -287,68 +310,83 @@ def _run_ours(args, rank, world, local):
 
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tensor pass, core factor) + f64",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16 tensor-core operands (f32 accumulate), f32 core factor, f64 control",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R, "tensor_dtype": "f32",
-                      "core": "f32 Gauss-Jordan inverse + f64 refinement (<= 8 sweeps, adaptive)", "l2": "flushed between steps",
+           "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R,
+                      "tensor_dtype": "bf16x2 (hi + lo bfloat16 planes, 16 significant bits)",
+                      "core": "f32 Gauss-Jordan inverse + f64 refinement (<= 8 sweeps, adaptive)",
+                      "l2": "flushed between steps",
                       "parallelism": f"replicas x{world}", "global_batch": world},
            "gpu_launches": nk * args.steps, "clocks": clk.summary(),
            "state_after": {k: status[k] for k in ("iters", "accepted", "rel_err", "mu", "stop_reason",
                                                   "refine_resid")}}
 
     if not args.no_extras and rank == 0:
-        # --- MTTKRP pass alone (the tensor-touching kernel) against HBM ---
-        ws = cp.alloc_workspace(shape32)
-        a_in = cp.factors_to_device(prob32.init)
-        m = torch.empty_like(a_in)
-        r2 = torch.empty(1, dtype=torch.float64, device="cuda")
-        for _ in range(3):
-            cp._lib.cp_mttkrp_all(cp.ctypes.byref(shape32), cp._ptr(Y32), cp._ptr(a_in), cp._ptr(m),
-                                  cp._ptr(r2), cp._ptr(ws), ws.numel(), cp._stream())
-        evs = []
-        for _ in range(20):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            cp._lib.cp_mttkrp_all(cp.ctypes.byref(shape32), cp._ptr(Y32), cp._ptr(a_in), cp._ptr(m),
-                                  cp._ptr(r2), cp._ptr(ws), ws.numel(), cp._stream())
-            e1.record()
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        mt_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+        # --- the tensor pass alone against HBM: this workload and a large one ---
+        a_in = cp.factors_to_device(prob.init)
+        mt_ms = time_pass(shape2, Y2, a_in)
         bytes_alg = int(np.prod(DIMS)) * 4
         achieved = bytes_alg / (mt_ms * 1e-3) / 1e9
-        out["roofline"] = {"bound": "hbm", "kernel": "k_mttkrp3<float,*> (all-mode MTTKRP + direct residual, one pass)",
+        out["roofline"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3 (all-mode MTTKRP + direct residual, one pass)",
                            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                            "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": mt_ms,
-                           "algorithmic_bytes": bytes_alg}
+                           "algorithmic_bytes": bytes_alg, "peak_kind": "burst (kernel timed alone)"}
+        big = (512, 512, 512)
+        gbig = torch.Generator(device="cuda").manual_seed(seed)
+        Ybig = cp.tensor_split(torch.randn(int(np.prod(big)), generator=gbig, device="cuda", dtype=torch.float32))
+        abig = torch.randn(32 * sum(big), generator=gbig, device="cuda", dtype=torch.float64)
+        sbig = cp.make_shape(big, 32, "bf16x2")
+        big_ms = time_pass(sbig, Ybig, abig)
+        bbig = int(np.prod(big)) * 4
+        out["roofline_large"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3", "workload": "512^3, R=32, bf16x2",
+                                 "achieved": bbig / (big_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": bbig / (big_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                 "ms_per_launch": big_ms, "algorithmic_bytes": bbig}
+        del Ybig, abig
+        # the float32-tensor form of the same step (tensor-core pass with an
+        # exact float32 residual)
+        prob32 = synth.config2(seed, DIMS, dtype="f32")
+        shape32 = cp.make_shape(DIMS, R, "f32")
+        Y32 = cp.tensor_to_device(prob32.Y, "f32")
+        st32, _ = new_state(shape32, cp.CP_CORE_MIXED, prob32.init)
+        st32.init(Y32)
+        k32 = max(5, args.steps // 2)
+        t32, _ = timed_steps(st32, Y32, k32, 2)
+        out["f32_tensor_form"] = {"value": k32 / (t32 / 1e3), "unit": "iters/s", "ms_per_step": t32 / k32,
+                                  "mttkrp_ms": time_pass(shape32, Y32, cp.factors_to_device(prob32.init))}
+        st32.close()
 
-        # --- end to end through the public API with host buffers ---
-        Yh = Y32.cpu().pin_memory()
-        Yd = torch.empty_like(Y32)
-        st_e, _ = new_state(shape32, cp.CP_CORE_MIXED, prob32.init)
-        Yd.copy_(Yh)
-        st_e.init(Yd)
+        # --- end to end through the public API: float32 tensor on the host ---
+        Yh = torch.from_numpy(np.asarray(prob.Y, dtype=np.float32).ravel(order="F")).pin_memory()
+        Yd32 = torch.empty(Yh.numel(), dtype=torch.float32, device="cuda")
+        Yd2 = torch.empty(2 * Yh.numel(), dtype=torch.bfloat16, device="cuda")
+        st_e, _ = new_state(shape2, cp.CP_CORE_MIXED, prob.init)
+        Yd32.copy_(Yh)
+        cp.tensor_split(Yd32, out=Yd2)
+        st_e.init(Yd2)
         for _ in range(args.warmup):
-            st_e.step(Yd)
+            st_e.step(Yd2)
         hst = torch.empty(128, dtype=torch.uint8).pin_memory()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
-            Yd.copy_(Yh, non_blocking=True)
-            st_e.step(Yd)
+            Yd32.copy_(Yh, non_blocking=True)
+            cp.tensor_split(Yd32, out=Yd2)
+            st_e.step(Yd2)
             hst.copy_(st_e.status_tensor(), non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1)
         out["e2e"] = {"value": args.steps / (e2e_ms / 1e3), "unit": "iters/s",
-                      "h2d_bytes_per_step": Yh.numel() * Yh.element_size(), "d2h_bytes_per_step": 128}
+                      "h2d_bytes_per_step": Yh.numel() * Yh.element_size(), "d2h_bytes_per_step": 128,
+                      "path": "pinned float32 host tensor -> device, cp_tensor_split, cp_dgn_step, status -> host"}
         st_e.close()
 
         # --- plain float64 form on the float64 tensor ---
-        prob64 = synth.config2(seed, DIMS, dtype="f64")
+        prob64 = prob                  # the same tensor values, stored as float64
         shape64 = cp.make_shape(DIMS, R, "f64")
         Y64 = cp.tensor_to_device(prob64.Y, "f64")
         st64, _ = new_state(shape64, cp.CP_CORE_F64, prob64.init)
@@ -376,10 +414,11 @@ def _run_ours(args, rank, world, local):
             s.close()
             return {"seconds": t, "iters": d["iters"], "accepted": d["accepted"], "rel_err": d["rel_err"],
                     "stop": d["stop_reason"]}
-        ttf32 = ttf(shape32, Y32, prob32, cp.CP_CORE_MIXED)
+        ttf2 = ttf(shape2, Y2, prob, cp.CP_CORE_MIXED)
         ttf64 = ttf(shape64, Y64, prob64, cp.CP_CORE_F64)
-        out["time_to_fit"] = {"mixed_f32": ttf32, "plain_f64": ttf64,
-                              "gain": ttf64["seconds"] / ttf32["seconds"]}
+        out["time_to_fit"] = {"mixed": ttf2, "plain_f64": ttf64,
+                              "gain": ttf64["seconds"] / ttf2["seconds"],
+                              "rel_err_diff": abs(ttf2["rel_err"] - ttf64["rel_err"]) / ttf64["rel_err"]}
 
         if not args.no_batch:
             out["batched"] = bench_batched(seed)
@@ -387,11 +426,11 @@ def _run_ours(args, rank, world, local):
             out["served"] = bench_served(seed, args.serve_seconds, args.serve_rate)
 
         # --- CPU oracle on the host cores (bounded sample) ---
-        rate, iters, secs = oracle_rate(prob32, args.cpu_seconds)
+        rate, iters, secs = oracle_rate(prob, args.cpu_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": "iters/s", "cores": oracle_threads(),
                                "kind": "oracle",
                                "sample": f"first {iters} LM iterations of the same 200^3 R=20 problem "
-                                         f"(float32-rounded tensor in float64), {secs:.1f} s"}
+                                         f"(the same tensor values in float64), {secs:.1f} s"}
     st.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -501,6 +540,9 @@ def bench_served(seed, seconds, rate):
         r = srv.serve([req], realtime=False)[0]
         t32 = time.perf_counter() - t32
         y64, a64 = S.synth_on_device(req, srv.device, torch.float64)
+        if S.two_plane_ok(d, R):          # the served request ran on the hi + lo values
+            y2 = cp.tensor_split(y64.float())
+            y64 = y2[:y64.numel()].double() + y2[y64.numel():].double()
         dt, d64 = _ttf_state(cp, cp.make_shape(d, R, "f64"), y64, a64, cp.CP_CORE_F64, tol=1e-8)
         alone["x".join(map(str, d)) + f"-R{R}"] = {"mixed_s": t32, "mixed_iters": r.status["iters"],
                                                   "f64_s": dt, "f64_iters": d64["iters"], "gain": dt / t32}
@@ -520,7 +562,7 @@ def run_reference(args):
         return
     from oracle import cp_oracle as O
     from paper_1205_2584_gb300 import synth
-    prob = synth.config2(args.seed, DIMS, dtype="f32")
+    prob = synth.config2(args.seed, DIMS, dtype="bf16x2")
     # warm-up iterations, then K timed LM iterations continuing from there
     w = O.lm_fit(prob.Y, prob.init, mu0=None, max_iter=max(1, args.warmup), tol=0.0)
     t0 = time.perf_counter()
@@ -531,7 +573,8 @@ def run_reference(args):
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R, "tensor_dtype": "f32-rounded, f64 math"},
+           "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R,
+                      "tensor_dtype": "bf16x2 values (hi + lo) in float64, f64 math"},
            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": oracle_threads(), "kind": "oracle",
                             "sample": f"{len(times)} consecutive LM iterations from the seeded start"},
            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -194,7 +194,7 @@ def lane_bytes(dims: Sequence[int], R: int) -> Optional[int]:
 def state_bytes(dims: Sequence[int], R: int) -> int:
     """Device bytes of one large request: tensor, factors, State workspace."""
     cp = _cp()
-    shape = cp.make_shape(dims, R, "f32")
+    shape = cp.make_shape(dims, R, "bf16x2" if two_plane_ok(dims, R) else "f32")
     return 4 * int(np.prod(dims)) + 8 * R * int(sum(dims)) + cp.workspace_bytes(shape, cp.CP_CORE_MIXED, True)
 
 
@@ -222,6 +222,11 @@ def synth_on_device(req: Request, device, dtype=None):
     a = torch.cat([torch.randn(I, req.R, generator=g, device=device, dtype=torch.float64).t().reshape(-1)
                    for I in req.dims])
     return y, a
+
+
+def two_plane_ok(dims: Sequence[int], R: int) -> bool:
+    """Shapes whose State runs on the two-plane bfloat16 tensor (tensor-core pass)."""
+    return len(dims) == 3 and int(dims[0]) % 8 == 0 and R <= 32
 
 
 def _inputs(req: Request, device):
@@ -342,20 +347,27 @@ class _StateSlot:
     and factor buffers, and a captured graph of `steps` steps).  A slot is
     re-armed for each request of its shape: the request's tensor and factors
     are copied into the slot's buffers and the state is re-initialised, so
-    the captured graph is reused."""
+    the captured graph is reused.  Where the shape allows, the tensor is held
+    as two bfloat16 planes (split once at admission) for the tensor-core pass."""
 
     def __init__(self, server, dims, R):
         import torch
         cp = _cp()
         self.dims, self.R = tuple(dims), int(R)
         self.bytes = state_bytes(dims, R)
+        self.two_plane = two_plane_ok(dims, R)
         dev = server.device
         self.stream = torch.cuda.Stream(device=dev)
         o = server.opts
+        J = int(np.prod(dims))
         with torch.cuda.stream(self.stream):
-            self.y = torch.zeros(int(np.prod(dims)), dtype=torch.float32, device=dev)
+            if self.two_plane:
+                self.y = torch.zeros(2 * J, dtype=torch.bfloat16, device=dev)
+            else:
+                self.y = torch.zeros(J, dtype=torch.float32, device=dev)
             self.a = torch.zeros(R * int(sum(dims)), dtype=torch.float64, device=dev)
-            self.state = cp.State(cp.make_shape(dims, R, "f32"), self.a, mu0=-1.0, tau=o.tau, tol=o.tol,
+            dtype = "bf16x2" if self.two_plane else "f32"
+            self.state = cp.State(cp.make_shape(dims, R, dtype), self.a, mu0=-1.0, tau=o.tau, tol=o.tol,
                                   mu_max=o.mu_max, max_iter=o.max_iter, normalize=bool(o.normalize),
                                   core_mode=cp.CP_CORE_MIXED, refine_iters=server.large_refine)
             self.state.capture(self.y, server.large_steps, stream=self.stream)
@@ -368,7 +380,10 @@ class _StateSlot:
         import torch
         with torch.cuda.stream(self.stream):
             y, a = _inputs(req, server.device)
-            self.y.copy_(y)
+            if self.two_plane:
+                _cp().tensor_split(y.contiguous(), out=self.y, stream=self.stream)
+            else:
+                self.y.copy_(y)
             self.a.copy_(a)
             self.state.init(self.y, stream=self.stream)
         self.req = req

@@ -18,20 +18,23 @@ def sv():
     return serve
 
 
-def _req(serve, rid, seed, dims, R, arrival=0.0):
-    p = synth.make_problem(seed, dims, R, dtype="f32", snr_db=30.0, collinearity=(0.8,))
+def _req(serve, rid, seed, dims, R, arrival=0.0, dtype="f32"):
+    p = synth.make_problem(seed, dims, R, dtype=dtype, snr_db=30.0, collinearity=(0.8,))
     return serve.Request(rid=rid, arrival=arrival, dims=tuple(dims), R=R, Y=p.Y, init=p.init), p
 
 
 SMALL = [((20, 22, 18), 4), ((32, 32, 32), 5), ((16, 30, 12), 3), ((40, 12, 25), 6)]
 MEDIUM = [((64, 64, 64), 12), ((96, 50, 40), 16)]
 LARGE = [((300, 24, 20), 4)]          # I_1 > 256: outside the batched kernel
+# I_1 > 256 and a multiple of 8: a State on the two-plane bfloat16 tensor; its
+# values are drawn two-plane representable, so the oracle sees the same tensor
+LARGE2 = [((264, 24, 20), 4)]
 
 
 def _mix(serve):
     reqs, probs = [], []
-    for k, (dims, R) in enumerate(SMALL + MEDIUM + LARGE):
-        r, p = _req(serve, k, 900 + k, dims, R)
+    for k, (dims, R) in enumerate(SMALL + MEDIUM + LARGE + LARGE2):
+        r, p = _req(serve, k, 900 + k, dims, R, dtype="bf16x2" if (dims, R) in LARGE2 else "f32")
         reqs.append(r)
         probs.append(p)
     return reqs, probs
@@ -68,12 +71,12 @@ def test_large_request_alone_and_in_mix_agree(sv):
     srv = _server(sv)
     mixed = {r.rid: r for r in srv.serve(reqs, realtime=False)}
     srv.close()
-    k = len(reqs) - 1
-    srv = _server(sv)
-    alone = srv.serve([reqs[k]], realtime=False)[0]
-    srv.close()
-    assert mixed[k].path == alone.path == "state"
-    assert mixed[k].status["rel_err"] == pytest.approx(alone.status["rel_err"], rel=1e-6)
+    for k in (len(SMALL + MEDIUM), len(reqs) - 1):     # float32 and two-plane State requests
+        srv = _server(sv)
+        alone = srv.serve([reqs[k]], realtime=False)[0]
+        srv.close()
+        assert mixed[k].path == alone.path == "state"
+        assert mixed[k].status["rel_err"] == pytest.approx(alone.status["rel_err"], rel=1e-6)
 
 
 def test_served_fits_match_oracle(sv):
@@ -81,7 +84,7 @@ def test_served_fits_match_oracle(sv):
     srv = _server(sv)
     got = {r.rid: r for r in srv.serve(reqs, realtime=False)}
     srv.close()
-    for k in (0, 2, 4, len(reqs) - 1):
+    for k in (0, 2, 4, len(reqs) - 2, len(reqs) - 1):
         ref = O.lm_fit(probs[k].Y, probs[k].init, mu0=None, max_iter=300, tol=1e-8)
         assert got[k].status["stop"] != 0
         assert got[k].status["rel_err"] == pytest.approx(ref.rel_err, rel=1e-6), (k, got[k].status, ref.rel_err)
