@@ -43,6 +43,10 @@ DIMS = (200, 200, 200)
 R = 20
 WORKLOAD = "cp3-200^3-R20-collinear(0.95,0.81,0.81)-snr40"
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_mttkrp_tc3 launch, from
+# the ncu captures summarised in profiles/k_mttkrp_tc3_bf16x2.md (bytes)
+TRAFFIC_200 = 32.293376e6
+TRAFFIC_512 = 537.939712e6 + 3.137536e6
 
 
 def parse():
@@ -183,13 +187,23 @@ def barrier(world):
 
 
 def allmax(x: float, world: int) -> float:
+    """Largest value over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(t_ms_local: float, steps: int, world: int):
+    """Whole-job throughput of `world` replicas that each ran `steps` steps:
+    all steps over the slowest rank's time (weak scaling).  Returns
+    (iters/s, ms per step, max time in ms)."""
+    t_ms = allmax(t_ms_local, world)
+    return world * steps / (t_ms / 1e3), t_ms / steps, t_ms
 
 
 def oracle_threads():
@@ -304,9 +318,7 @@ def _run_ours(args, rank, world, local):
     with ClockSampler(local) as clk:
         t_ms, nk = timed_steps(st, Y2, args.steps, args.warmup)
     status = st.status()
-    t_ms = allmax(t_ms, world)
-    ms_per_step = t_ms / args.steps
-    value = world * args.steps / (t_ms / 1e3)
+    value, ms_per_step, t_ms = aggregate(t_ms, args.steps, world)
 
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -330,7 +342,7 @@ def _run_ours(args, rank, world, local):
         achieved = bytes_alg / (mt_ms * 1e-3) / 1e9
         out["roofline"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3 (all-mode MTTKRP + direct residual, one pass)",
                            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                           "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                           "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_200,
                            "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": mt_ms,
                            "algorithmic_bytes": bytes_alg, "peak_kind": "burst (kernel timed alone)"}
         big = (512, 512, 512)
@@ -343,7 +355,7 @@ def _run_ours(args, rank, world, local):
         out["roofline_large"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3", "workload": "512^3, R=32, bf16x2",
                                  "achieved": bbig / (big_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": bbig / (big_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                                 "ms_per_launch": big_ms, "algorithmic_bytes": bbig}
+                                 "ms_per_launch": big_ms, "algorithmic_bytes": bbig, "traffic": TRAFFIC_512}
         del Ybig, abig
         # the float32-tensor form of the same step (tensor-core pass with an
         # exact float32 residual)
