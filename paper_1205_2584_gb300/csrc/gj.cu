@@ -9,51 +9,105 @@
 //     B[i,j] = A[i,j] - A[i,k] B[k,j]       (i, j != k)   k_gj_update
 // and after the last panel B = A^{-1}.  No pivoting is needed for an SPD
 // matrix (each pivot block is a Schur complement of an SPD matrix).  P^{-1}
-// is computed once per sweep by one CTA that keeps the block in registers;
-// for sweeps after the first, the CTA of k_gj_update that produces the next
-// pivot tile inverts it before it exits.  A and B alternate between sweeps.
-// A non-positive or non-finite pivot sets *info (1-based row); nothing traps.
+// of sweep k + 1 is computed during sweep k by one CTA (k_gj_pivot_next) on a
+// side stream.  A and B alternate between sweeps.  A non-positive or
+// non-finite pivot sets *info (1-based row); nothing traps.
+//
+// Every tile kernel runs 256 threads on a 64 x 64 tile; thread (bi, bj) owns
+// rows 4 bi .. 4 bi + 3 and columns 4 bj .. 4 bj + 3, so each k-step of a
+// tile product reads one float4 of the left operand (stored column by column,
+// rows contiguous) and one float4 of the right operand (stored row by row)
+// for 16 multiply-adds.
 #include "common.cuh"
 
 namespace cpdgn {
 
 constexpr int GJB = 64;           // panel / tile width
-constexpr int GJT = 256;          // threads per CTA: a 16 x 16 grid of 4 x 4 blocks
-constexpr int GJL = GJB + 1;      // padded leading dimension in shared memory
+constexpr int GJT = 256;          // threads per CTA: 16 x 16 threads, 4 x 4 entries each
+constexpr int GJP = GJB + 4;      // padded row length in shared memory (keeps float4 alignment)
 
 // Reciprocal of a pivot.  The float32 inverse only preconditions the float64
 // refinement, so the fast intrinsic division (about 2 ulp) is accurate enough.
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-template <typename T>
-__device__ void load_tile(const T* A, int64_t n, int ti, int tj, T (*S)[GJL]) {
-  constexpr int K = GJB * GJB / GJT;
-  T v[K];
+// S[c][r] = A(64 ti + r, 64 tj + c) (zero outside n x n): columns of the tile,
+// rows contiguous.  Global reads are coalesced along r.
+__device__ __forceinline__ void load_cols(const float* A, int64_t n, int ti, int tj, float (*S)[GJP]) {
 #pragma unroll
-  for (int q = 0; q < K; ++q) {
+  for (int q = 0; q < GJB * GJB / GJT; ++q) {
     const int e = int(threadIdx.x) + q * GJT;
-    const int i = e % GJB, j = e / GJB;
-    const int64_t r = int64_t(ti) * GJB + i, c = int64_t(tj) * GJB + j;
-    v[q] = (r < n && c < n) ? A[r + n * c] : T(0);
-  }
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    const int e = int(threadIdx.x) + q * GJT;
-    S[e % GJB][e / GJB] = v[q];
+    const int r = e % GJB, c = e / GJB;
+    const int64_t gr = int64_t(ti) * GJB + r, gc = int64_t(tj) * GJB + c;
+    S[c][r] = (gr < n && gc < n) ? A[gr + n * gc] : 0.f;
   }
 }
 
-template <typename T>
-__device__ void store_regs(const T (&x)[4][4], T* B, int64_t n, int ti, int tj) {
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+// S[r][c] = A(64 ti + r, 64 tj + c): rows of the tile, columns contiguous.
+__device__ __forceinline__ void load_rows(const float* A, int64_t n, int ti, int tj, float (*S)[GJP]) {
 #pragma unroll
-  for (int v = 0; v < 4; ++v)
+  for (int q = 0; q < GJB * GJB / GJT; ++q) {
+    const int e = int(threadIdx.x) + q * GJT;
+    const int r = e % GJB, c = e / GJB;
+    const int64_t gr = int64_t(ti) * GJB + r, gc = int64_t(tj) * GJB + c;
+    S[r][c] = (gr < n && gc < n) ? A[gr + n * gc] : 0.f;
+  }
+}
+
+// the thread's 4 x 4 block of tile (ti, tj); rows beyond n read as 0
+__device__ __forceinline__ void load_block(const float* A, int64_t n, int ti, int tj, float (&x)[4][4]) {
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+  const int64_t r0 = int64_t(ti) * GJB + 4 * bi;
+  const bool vec = (n % 4 == 0) && (r0 + 3 < n);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t r = int64_t(ti) * GJB + tx + 16 * u, c = int64_t(tj) * GJB + ty + 16 * v;
-      if (r < n && c < n) B[r + n * c] = x[u][v];
+  for (int v = 0; v < 4; ++v) {
+    const int64_t c = int64_t(tj) * GJB + 4 * bj + v;
+    if (c >= n) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u][v] = 0.f;
+    } else if (vec) {
+      const float4 t = *reinterpret_cast<const float4*>(A + r0 + n * c);
+      x[0][v] = t.x;
+      x[1][v] = t.y;
+      x[2][v] = t.z;
+      x[3][v] = t.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u][v] = (r0 + u < n) ? A[r0 + u + n * c] : 0.f;
     }
+  }
+}
+
+__device__ __forceinline__ void store_block(const float (&x)[4][4], float* B, int64_t n, int ti, int tj) {
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+  const int64_t r0 = int64_t(ti) * GJB + 4 * bi;
+  const bool vec = (n % 4 == 0) && (r0 + 3 < n);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int64_t c = int64_t(tj) * GJB + 4 * bj + v;
+    if (c >= n) continue;
+    if (vec) {
+      *reinterpret_cast<float4*>(B + r0 + n * c) = make_float4(x[0][v], x[1][v], x[2][v], x[3][v]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r0 + u < n) B[r0 + u + n * c] = x[u][v];
+    }
+  }
+}
+
+// x (+)= sgn * L R with L = Lc (columns, rows contiguous) and R = Rr (rows).
+__device__ __forceinline__ void tile_fma(const float (*Lc)[GJP], const float (*Rr)[GJP], float sgn, float (&x)[4][4]) {
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+#pragma unroll 8
+  for (int l = 0; l < GJB; ++l) {
+    const float4 a = *reinterpret_cast<const float4*>(&Lc[l][4 * bi]);
+    const float4 b = *reinterpret_cast<const float4*>(&Rr[l][4 * bj]);
+    const float av[4] = {sgn * a.x, sgn * a.y, sgn * a.z, sgn * a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) x[u][v] = fmaf(av[u], bv[v], x[u][v]);
+  }
 }
 
 // Row panel: B[k,j] = P^{-1} A[k,j] for j != k; CTA = tile column j.
@@ -61,31 +115,20 @@ template <typename T>
 __global__ void __launch_bounds__(GJT) k_gj_rowpanel(const T* A, T* B, int64_t n, int k, const T* Pinv,
                                                      const int* skip) {
   if (skip && *skip) return;
-  __shared__ T Ps[GJB][GJL], Xs[GJB][GJL];
+  __shared__ __align__(16) float Ps[GJB][GJP], Xs[GJB][GJP];
   const int nt = int((n + GJB - 1) / GJB);
   const int tj = blockIdx.x >= k ? blockIdx.x + 1 : blockIdx.x;
   if (tj >= nt) return;
-  load_tile(Pinv, GJB, 0, 0, Ps);
-  load_tile(A, n, k, tj, Xs);
-  __syncthreads();
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
+  load_cols(Pinv, GJB, 0, 0, Ps);
+  load_rows(A, n, k, tj, Xs);
+  float acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-  for (int l = 0; l < GJB; ++l) {
-    T a[4], b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) a[u] = Ps[tx + 16 * u][l];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) b[v] = Xs[l][ty + 16 * v];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
-  }
-  store_regs(acc, B, n, k, tj);
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  __syncthreads();
+  tile_fma(Ps, Xs, 1.f, acc);
+  store_block(acc, B, n, k, tj);
 }
 
 // Update of every tile outside row k.  When skip_pivot is set, tile
@@ -94,40 +137,27 @@ template <typename T>
 __global__ void __launch_bounds__(GJT) k_gj_update(const T* A, T* B, int64_t n, int k, const T* Pinv,
                                                    int skip_pivot, const int* skip) {
   if (skip && *skip) return;
-  __shared__ T Ls[GJB][GJL], Rs[GJB][GJL];
+  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP];
   const int nt = int((n + GJB - 1) / GJB);
   const int b = int(blockIdx.x);
   const int ti = b % (nt - 1) >= k ? b % (nt - 1) + 1 : b % (nt - 1);
   const int tj = b / (nt - 1);
   if (skip_pivot && ti == k + 1 && tj == k + 1) return;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  load_tile(A, n, ti, k, Ls);                        // A[i,k]
+  load_cols(A, n, ti, k, Ls);                        // A[i,k]
+  if (tj == k) load_rows(Pinv, GJB, 0, 0, Rs);
+  else load_rows(B, n, k, tj, Rs);                   // B[k,j] from the row panel
+  float acc[4][4];
   if (tj == k) {
-    load_tile(Pinv, GJB, 0, 0, Rs);
-  } else {
-    load_tile(B, n, k, tj, Rs);                      // B[k,j] from the row panel
-  }
-  T acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int64_t r = int64_t(ti) * GJB + tx + 16 * u, c = int64_t(tj) * GJB + ty + 16 * v;
-      acc[u][v] = (tj == k || r >= n || c >= n) ? T(0) : A[r + n * c];
-    }
-  __syncthreads();
-  for (int l = 0; l < GJB; ++l) {
-    T a[4], bb[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) a[u] = Ls[tx + 16 * u][l];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) bb[v] = Rs[l][ty + 16 * v];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = fma(-a[u], bb[v], acc[u][v]);
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  } else {
+    load_block(A, n, ti, tj, acc);
   }
-  store_regs(acc, B, n, ti, tj);
+  __syncthreads();
+  tile_fma(Ls, Rs, -1.f, acc);
+  store_block(acc, B, n, ti, tj);
 }
 
 // The first kb0 tiles of the core lie inside its leading identity block
@@ -139,191 +169,166 @@ __global__ void __launch_bounds__(GJT) k_gj_update(const T* A, T* B, int64_t n, 
 template <typename T>
 __global__ void __launch_bounds__(GJT) k_gj_identity(const T* A, T* B, int64_t n, int kb0, const int* skip) {
   if (skip && *skip) return;
-  __shared__ T Ls[GJB][GJL], Rs[GJB][GJL];
+  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP];
   const int nt = int((n + GJB - 1) / GJB);
   const int ti = blockIdx.x % nt, tj = blockIdx.x / nt;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+  float acc[4][4];
   if (ti < kb0 || tj < kb0) {
-    const T sgn = (ti >= kb0) ? T(-1) : T(1);
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int64_t r = int64_t(ti) * GJB + tx + 16 * u, c = int64_t(tj) * GJB + ty + 16 * v;
-        if (ti < kb0 && tj < kb0) acc[u][v] = (r == c) ? T(1) : T(0);
-        else acc[u][v] = (r < n && c < n) ? sgn * A[r + n * c] : T(0);
-      }
-    store_regs(acc, B, n, ti, tj);
-    return;
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int64_t r = int64_t(ti) * GJB + tx + 16 * u, c = int64_t(tj) * GJB + ty + 16 * v;
-      acc[u][v] = (r < n && c < n) ? A[r + n * c] : T(0);
-    }
-  for (int kk = 0; kk < kb0; ++kk) {
-    __syncthreads();
-    load_tile(A, n, ti, kk, Ls);
-    load_tile(A, n, kk, tj, Rs);
-    __syncthreads();
-    for (int l = 0; l < GJB; ++l) {
-      T a[4], bb[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = Ls[tx + 16 * u][l];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) bb[v] = Rs[l][ty + 16 * v];
+    if (ti < kb0 && tj < kb0) {
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(-a[u], bb[v], acc[u][v]);
+        for (int v = 0; v < 4; ++v)
+          acc[u][v] = (int64_t(ti) * GJB + 4 * bi + u == int64_t(tj) * GJB + 4 * bj + v) ? 1.f : 0.f;
+    } else {
+      load_block(A, n, ti, tj, acc);
+      if (ti >= kb0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = -acc[u][v];
+      }
     }
+    store_block(acc, B, n, ti, tj);
+    return;
   }
-  store_regs(acc, B, n, ti, tj);
+  load_block(A, n, ti, tj, acc);
+  for (int kk = 0; kk < kb0; ++kk) {
+    __syncthreads();
+    load_cols(A, n, ti, kk, Ls);
+    load_rows(A, n, kk, tj, Rs);
+    __syncthreads();
+    tile_fma(Ls, Rs, -1.f, acc);
+  }
+  store_block(acc, B, n, ti, tj);
 }
 
 // ---------------------------------------------------------------------------
-// The pivot chain is the sequential part of the inversion, so each pivot is
-// inverted by one 1024-thread CTA (32 x 32 threads, a 2 x 2 register block
-// each: ~20 instructions and 8 resident warps per scheduler per elimination
-// step).  For sweep k + 1 the same CTA first forms its pivot tile
-// X = A[k+1,k+1] - A[k+1,k] B[k,k+1] (B[k,:] is sweep k's row panel), so it
-// can run concurrently with sweep k's update of every other tile.
+// The pivot chain is the sequential part of the inversion.  Each pivot block
+// is inverted by one 256-thread CTA that keeps the block in registers (4 x 4
+// entries per thread); an elimination step broadcasts the pivot row and
+// column through shared memory (one float4 each per thread).  For sweep k + 1
+// the same CTA first forms its pivot tile X = A[k+1,k+1] - A[k+1,k] B[k,k+1]
+// (B[k,:] is sweep k's row panel), so it runs concurrently with sweep k's
+// update of every other tile.
 // ---------------------------------------------------------------------------
-constexpr int PVT = 1024;
-
-template <typename T>
-__device__ void gj_invert_2x2(T (&x)[2][2], int kb, T (*prow)[GJB], T (*pcol)[GJB], int* bad) {
-  __shared__ T pv[GJB];                                          // pivots, checked at the end
-  const int tid = threadIdx.x, bi = tid % 32, bj = tid / 32;   // rows 2 bi + u, cols 2 bj + v
-#pragma unroll 2
+__device__ void gj_invert_tile(float (&x)[4][4], int kb, float (*prow)[GJB], float (*pcol)[GJB], int* bad) {
+  __shared__ float pv[GJB];                                    // pivots, checked at the end
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+#pragma unroll 4
   for (int p = 0; p < kb; ++p) {
     const int par = p & 1;
-    const int hp = p >> 1, lp = p & 1;
+    const int hp = p >> 2, lp = p & 3;
     if (bi == hp) {
-      prow[par][2 * bj] = lp ? x[1][0] : x[0][0];
-      prow[par][2 * bj + 1] = lp ? x[1][1] : x[0][1];
+      float4 t;
+      t.x = x[lp][0];
+      t.y = x[lp][1];
+      t.z = x[lp][2];
+      t.w = x[lp][3];
+      *reinterpret_cast<float4*>(&prow[par][4 * bj]) = t;
     }
     if (bj == hp) {
-      pcol[par][2 * bi] = lp ? x[0][1] : x[0][0];
-      pcol[par][2 * bi + 1] = lp ? x[1][1] : x[1][0];
+      float4 t;
+      t.x = x[0][lp];
+      t.y = x[1][lp];
+      t.z = x[2][lp];
+      t.w = x[3][lp];
+      *reinterpret_cast<float4*>(&pcol[par][4 * bi]) = t;
     }
     __syncthreads();
-    const T piv = prow[par][p];
-    if (tid == 0) pv[p] = piv;
-    const T dinv = recip(piv);
-    const T c0 = pcol[par][2 * bi], c1 = pcol[par][2 * bi + 1];
-    const T r0 = prow[par][2 * bj] * dinv, r1 = prow[par][2 * bj + 1] * dinv;
-    x[0][0] = fma(-c0, r0, x[0][0]);
-    x[0][1] = fma(-c0, r1, x[0][1]);
-    x[1][0] = fma(-c1, r0, x[1][0]);
-    x[1][1] = fma(-c1, r1, x[1][1]);
+    const float piv = prow[par][p];
+    if (threadIdx.x == 0) pv[p] = piv;
+    const float dinv = recip(piv);
+    const float4 c4 = *reinterpret_cast<const float4*>(&pcol[par][4 * bi]);
+    const float4 r4 = *reinterpret_cast<const float4*>(&prow[par][4 * bj]);
+    const float c[4] = {c4.x, c4.y, c4.z, c4.w};
+    const float r[4] = {r4.x * dinv, r4.y * dinv, r4.z * dinv, r4.w * dinv};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) x[u][v] = fmaf(-c[u], r[v], x[u][v]);
     if (bi == hp) {                  // row p -> scaled pivot row
-      if (lp) { x[1][0] = r0; x[1][1] = r1; }
-      else { x[0][0] = r0; x[0][1] = r1; }
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (lp == 0) x[0][v] = r[v];
+        else if (lp == 1) x[1][v] = r[v];
+        else if (lp == 2) x[2][v] = r[v];
+        else x[3][v] = r[v];
     }
     if (bj == hp) {                  // column p -> -col / piv; the pivot itself -> 1 / piv
-      if (lp) {
-        x[0][1] = -c0 * dinv;
-        x[1][1] = (bi == hp) ? dinv : -c1 * dinv;
-      } else {
-        x[0][0] = (bi == hp) ? dinv : -c0 * dinv;
-        x[1][0] = -c1 * dinv;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float val = (bi == hp && u == lp) ? dinv : -c[u] * dinv;
+        if (lp == 0) x[u][0] = val;
+        else if (lp == 1) x[u][1] = val;
+        else if (lp == 2) x[u][2] = val;
+        else x[u][3] = val;
       }
     }
   }
   // check the recorded pivots once, after the elimination
   __syncthreads();
-  if (tid < kb && !(pv[tid] > T(0) && isfinite(pv[tid]))) atomicMin(bad, tid + 1);
+  if (threadIdx.x < kb && !(pv[threadIdx.x] > 0.f && isfinite(pv[threadIdx.x]))) atomicMin(bad, threadIdx.x + 1);
   __syncthreads();
 }
 
-// Tile (ti, tj) of A as 2 x 2 register blocks (identity beyond kb).
-template <typename T>
-__device__ void load_2x2(const T* A, int64_t n, int ti, int tj, int kb, T (&x)[2][2]) {
-  const int bi = threadIdx.x % 32, bj = threadIdx.x / 32;
+// rows/columns of a partial pivot tile beyond kb become the identity
+__device__ __forceinline__ void pad_identity(float (&x)[4][4], int kb) {
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const int i = 2 * bi + u, j = 2 * bj + v;
-      const int64_t r = int64_t(ti) * GJB + i, c = int64_t(tj) * GJB + j;
-      x[u][v] = (i < kb && j < kb) ? A[r + n * c] : (i == j ? T(1) : T(0));
-    }
+    for (int v = 0; v < 4; ++v)
+      if (4 * bi + u >= kb || 4 * bj + v >= kb) x[u][v] = (4 * bi + u == 4 * bj + v) ? 1.f : 0.f;
 }
 
-// Invert x (pivot tile kk) and write P^{-1} to Pinv and into tile (kk, kk) of D.
-template <typename T>
-__device__ void pivot_store(T (&x)[2][2], int64_t n, int kk, int kb, T* Pinv, T* D, int* info,
-                            T (*prow)[GJB], T (*pcol)[GJB], int* bad) {
-  const int bi = threadIdx.x % 32, bj = threadIdx.x / 32;
+// Invert x (pivot tile kk) and write P^{-1} to Pinv (64 x 64) and into tile
+// (kk, kk) of D.
+__device__ void pivot_store(float (&x)[4][4], int64_t n, int kk, int kb, float* Pinv, float* D, int* info,
+                            float (*prow)[GJB], float (*pcol)[GJB], int* bad) {
   if (threadIdx.x == 0) *bad = GJB + 1;
   __syncthreads();
-  gj_invert_2x2<T>(x, kb, prow, pcol, bad);
+  gj_invert_tile(x, kb, prow, pcol, bad);
   if (threadIdx.x == 0 && *bad <= GJB && info) atomicCAS(info, 0, kk * GJB + *bad);
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const int i = 2 * bi + u, j = 2 * bj + v;
-      Pinv[i + GJB * j] = x[u][v];
-      if (i < kb && j < kb) D[(int64_t(kk) * GJB + i) + n * (int64_t(kk) * GJB + j)] = x[u][v];
-    }
+  store_block(x, Pinv, GJB, 0, 0);
+  store_block(x, D, n, kk, kk);
 }
 
 // Pivot of sweep k (tile (k, k) of A as it stands); P^{-1} also into D's tile.
 template <typename T>
-__global__ void __launch_bounds__(PVT) k_gj_pivot(const T* A, T* D, int64_t n, int k, T* Pinv, int* info,
+__global__ void __launch_bounds__(GJT) k_gj_pivot(const T* A, T* D, int64_t n, int k, T* Pinv, int* info,
                                                   const int* skip) {
   if (skip && *skip) return;
-  __shared__ T prow[2][GJB], pcol[2][GJB];
+  __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
   __shared__ int bad;
   const int kb = int((n - int64_t(k) * GJB) < GJB ? (n - int64_t(k) * GJB) : GJB);
-  T x[2][2];
-  load_2x2(A, n, k, k, kb, x);
-  pivot_store<T>(x, n, k, kb, Pinv, D, info, prow, pcol, &bad);
+  float x[4][4];
+  load_block(A, n, k, k, x);
+  pad_identity(x, kb);
+  pivot_store(x, n, k, kb, Pinv, D, info, prow, pcol, &bad);
 }
 
 // Pivot of sweep k + 1 during sweep k: X = A[k+1,k+1] - A[k+1,k] B[k,k+1],
 // inverted; P^{-1} goes to Pinv_next and into A's tile (k+1, k+1), which sweep
 // k + 1 writes into and which nobody else reads during sweep k.
 template <typename T>
-__global__ void __launch_bounds__(PVT) k_gj_pivot_next(T* A, const T* B, int64_t n, int k, T* Pinv_next,
+__global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, const T* B, int64_t n, int k, T* Pinv_next,
                                                        int* info, const int* skip) {
   if (skip && *skip) return;
-  __shared__ T Ls[GJB][GJL], Rs[GJB][GJL];
-  __shared__ T prow[2][GJB], pcol[2][GJB];
+  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP];
+  __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
   __shared__ int bad;
   const int k1 = k + 1;
   const int kb = int((n - int64_t(k1) * GJB) < GJB ? (n - int64_t(k1) * GJB) : GJB);
-  for (int e = threadIdx.x; e < GJB * GJB; e += PVT) {
-    const int i = e % GJB, j = e / GJB;
-    const int64_t r = int64_t(k1) * GJB + i, c = int64_t(k) * GJB + j, rr = int64_t(k) * GJB + i,
-                  cc = int64_t(k1) * GJB + j;
-    Ls[i][j] = (r < n) ? A[r + n * c] : T(0);          // A[k+1, k]
-    Rs[i][j] = (cc < n) ? B[rr + n * cc] : T(0);       // B[k, k+1]
-  }
-  T x[2][2];
-  load_2x2(A, n, k1, k1, kb, x);
+  load_cols(A, n, k1, k, Ls);          // A[k+1, k]
+  load_rows(B, n, k, k1, Rs);          // B[k, k+1]
+  float x[4][4];
+  load_block(A, n, k1, k1, x);
   __syncthreads();
-  const int bi = threadIdx.x % 32, bj = threadIdx.x / 32;
-#pragma unroll 8
-  for (int l = 0; l < GJB; ++l) {
-    const T a0 = Ls[2 * bi][l], a1 = Ls[2 * bi + 1][l];
-    const T b0 = Rs[l][2 * bj], b1 = Rs[l][2 * bj + 1];
-    x[0][0] = fma(-a0, b0, x[0][0]);
-    x[0][1] = fma(-a0, b1, x[0][1]);
-    x[1][0] = fma(-a1, b0, x[1][0]);
-    x[1][1] = fma(-a1, b1, x[1][1]);
-  }
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int v = 0; v < 2; ++v)
-      if (2 * bi + u >= kb || 2 * bj + v >= kb) x[u][v] = (2 * bi + u == 2 * bj + v) ? T(1) : T(0);
-  pivot_store<T>(x, n, k1, kb, Pinv_next, A, info, prow, pcol, &bad);
+  tile_fma(Ls, Rs, -1.f, x);
+  pad_identity(x, kb);
+  pivot_store(x, n, k1, kb, Pinv_next, A, info, prow, pcol, &bad);
 }
 
 // Invert the n x n SPD matrix A (full storage, column-major); B is the second
@@ -346,7 +351,7 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
     src = dst;
     dst = t;
   }
-  k_gj_pivot<T><<<1, PVT, 0, s>>>(src, dst, n, k0, pinv + size_t(k0 & 1) * GJB * GJB, info, skip);
+  k_gj_pivot<T><<<1, GJT, 0, s>>>(src, dst, n, k0, pinv + size_t(k0 & 1) * GJB * GJB, info, skip);
   for (int k = k0; k < nt; ++k) {
     T* pk = pinv + size_t(k & 1) * GJB * GJB;
     T* pn = pinv + size_t((k + 1) & 1) * GJB * GJB;
@@ -356,14 +361,14 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
       if (next && side) {
         if (cudaEventRecord(ev_fork, s) != cudaSuccess) return CP_ECUDA;
         if (cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return CP_ECUDA;
-        k_gj_pivot_next<T><<<1, PVT, 0, side>>>(src, dst, n, k, pn, info, skip);
+        k_gj_pivot_next<T><<<1, GJT, 0, side>>>(src, dst, n, k, pn, info, skip);
         if (cudaEventRecord(ev_join, side) != cudaSuccess) return CP_ECUDA;
       }
       k_gj_update<T><<<(nt - 1) * nt, GJT, 0, s>>>(src, dst, n, k, pk, (next && side) ? 1 : 0, skip);
       if (next && side) {
         if (cudaStreamWaitEvent(s, ev_join, 0) != cudaSuccess) return CP_ECUDA;
       } else if (next) {
-        k_gj_pivot<T><<<1, PVT, 0, s>>>(dst, src, n, k + 1, pn, info, skip);
+        k_gj_pivot<T><<<1, GJT, 0, s>>>(dst, src, n, k + 1, pn, info, skip);
       }
     }
     T* t = src;
