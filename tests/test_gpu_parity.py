@@ -224,3 +224,31 @@ def test_full_size_config2_sampled(cp):
             ref = Yn[i] @ KR
             assert rel(mg[n][i].numpy(), ref) < 2e-5
     assert float(r2.item()) == pytest.approx(O.residual2(p.Y, p.init), rel=1e-5)
+
+
+def test_full_size_config3_sampled(cp):
+    """60^4, R = 15 (core N R^2 = 900), column norms log-uniform over
+    [1e-2, 1e2], SNR 30 dB, bfloat16 tensor (the 4-way SIMT pass): MTTKRP rows
+    sampled in every mode and the residual at full size against the oracle on
+    the same rounded tensor; then one mixed-precision step, whose trial
+    residual must equal the oracle's residual at the GPU's trial point."""
+    p = synth.config3(0)
+    shape, Y, a = setup(cp, p, "bf16")
+    m, r2 = cp.mttkrp_all(shape, Y, a)
+    mg = cp.split_factors(m.cpu(), p.dims, p.R)
+    rng = np.random.default_rng(11)
+    for n in range(4):
+        KR = O.kr_except(p.init, n)
+        Yn = O.unfold(p.Y, n)
+        for i in rng.integers(0, p.dims[n], size=3):
+            ref = Yn[i] @ KR
+            assert rel(mg[n][i].numpy(), ref) < 2e-5, (n, i)
+    assert float(r2.item()) == pytest.approx(O.residual2(p.Y, p.init), rel=1e-5)
+    st = cp.State(shape, a.clone(), mu0=-1.0, max_iter=5, core_mode=1, normalize=False)
+    st.init(Y)
+    st.step(Y)
+    torch.cuda.synchronize()
+    delta = cp.split_factors(st.buffer(cp.State.BUF_DELTA, p.R * sum(p.dims)).cpu(), p.dims, p.R)
+    trial = [a0 + d.numpy() for a0, d in zip(p.init, delta)]
+    assert st.status()["resid2_trial"] == pytest.approx(O.residual2(p.Y, trial), rel=1e-5)
+    assert st.status()["refine_resid"] < 1e-8
