@@ -60,6 +60,8 @@ struct BShared {
   float Mn[3 * 256 * BR];          // partial M_n, n >= 2 (sum_{n>=2} I_n R <= 3 * 256 * 16)
   float blk[BNB * (BNB + 1)];      // Cholesky diagonal block / solve block
   float vec[1024];                 // right-hand side of the float32 solves
+  int fix[(BN - 1) * TF];          // mode indices i_2.. of the tile's fibres
+  float Af[3 * 256 * BR];          // factor rows of modes 2.. (float32), same layout as Mn
 };
 
 __device__ double bsum(double v, double* red) {
@@ -91,29 +93,44 @@ __device__ double b_pass(const BCtx& c, BShared<TF>& sh, const double* A, double
   int64_t mn = 0;
   for (int k = 1; k < N; ++k) { moff[k] = mn; mn += c.I[k] * R; }
   for (int64_t e = tid; e < mn; e += BT) sh.Mn[e] = 0.f;
+  for (int k = 1; k < N; ++k) {                 // factor rows of modes 2.., row-major
+    const int Ik = int(c.I[k]);
+    for (int e = tid; e < Ik * R; e += BT) {
+      const int i = e / R, r = e % R;
+      sh.Af[moff[k] + e] = float(A[c.aoff[k] + i + int64_t(r) * Ik]);
+    }
+  }
   float acc[BR];
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = 0.f;
   double e2 = 0.0;
   __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
   for (int64_t f0 = 0; f0 < c.nfib; f0 += TF) {
     const int nf = int((c.nfib - f0) < TF ? (c.nfib - f0) : TF);
-    for (int e = tid; e < nf * I1; e += BT) {
-      const int f = e / I1, i = e % I1;
-      sh.Yt[f * ldy + i] = c.Y[(f0 + f) * I1 + i];
-    }
-    for (int e = tid; e < nf * R; e += BT) {
-      const int f = e / R, r = e % R;
-      int64_t rem = f0 + f;
-      float v[BN];
-      int idx[BN];
+    // the tile's fibres: mode indices once per fibre (32-bit: nfib < 2^31 here)
+    if (tid < nf) {
+      int rem = int(f0) + tid;
 #pragma unroll
       for (int k = 1; k < BN; ++k)
         if (k < N) {
-          idx[k] = int(rem % c.I[k]);
-          rem /= c.I[k];
-          v[k] = float(A[c.aoff[k] + idx[k] + int64_t(r) * c.I[k]]);
+          const int Ik = int(c.I[k]);
+          const int q = rem / Ik;
+          sh.fix[(k - 1) * TF + tid] = rem - q * Ik;
+          rem = q;
         }
+    }
+    for (int f = warp; f < nf; f += BT / 32) {
+      const float* src = c.Y + (f0 + f) * I1;
+      for (int i = lane; i < I1; i += 32) sh.Yt[f * ldy + i] = src[i];
+    }
+    __syncthreads();
+    for (int e = tid; e < nf * R; e += BT) {
+      const int f = e / R, r = e % R;
+      float v[BN];
+#pragma unroll
+      for (int k = 1; k < BN; ++k)
+        if (k < N) v[k] = sh.Af[moff[k] + sh.fix[(k - 1) * TF + f] * R + r];
       float kr = 1.f;
 #pragma unroll
       for (int k = 1; k < BN; ++k)
@@ -164,14 +181,9 @@ __device__ double b_pass(const BCtx& c, BShared<TF>& sh, const double* A, double
       __syncthreads();
       for (int e = tid; e < (N - 1) * R; e += BT) {
         const int k = 1 + e / R, r = e % R;
+        float* base = &sh.Mn[moff[k] + r];
         for (int f = 0; f < nf; ++f) {
-          int64_t rem = f0 + f;
-          int ik = 0;
-          for (int q = 1; q <= k; ++q) {
-            ik = int(rem % c.I[q]);
-            rem /= c.I[q];
-          }
-          float* dst = &sh.Mn[moff[k] + int64_t(ik) * R + r];
+          float* dst = base + sh.fix[(k - 1) * TF + f] * R;
           *dst = fmaf(sh.t[f * R + r], sh.loo[((k - 1) * TF + f) * R + r], *dst);
         }
       }
@@ -442,20 +454,30 @@ __device__ bool b_chol(const BCtx& c, BShared<TF>& sh) {
 // v <- (L L^T)^{-1} v with the float32 factor, v in sh.vec (length n <= 1024)
 template <int TF>
 __device__ void b_tri_solve(const BCtx& c, BShared<TF>& sh) {
+  // core = L L^T (float32, lower triangle in c.core): v <- L^{-T} L^{-1} v.
+  // Each 32 x 32 diagonal block is staged in shared memory; one warp walks
+  // it with the solution entries in registers (lane t holds entry k0 + t),
+  // then all threads apply the block to the remaining rows.
   const int n = c.n, tid = threadIdx.x;
   const float* A = c.core;
   float* v = sh.vec;
+  constexpr int L = BNB + 1;
   for (int k0 = 0; k0 < n; k0 += BNB) {          // forward: L z = v
     const int kb = (n - k0) < BNB ? (n - k0) : BNB;
     __syncthreads();
+    for (int e = tid; e < kb * kb; e += BT) {
+      const int i = e % kb, j = e / kb;
+      if (i >= j) sh.blk[i + L * j] = A[(k0 + i) + int64_t(n) * (k0 + j)];
+    }
+    __syncthreads();
     if (tid < 32) {
+      float vi = (tid < kb) ? v[k0 + tid] : 0.f;
       for (int p = 0; p < kb; ++p) {
-        __syncwarp();
-        const float zp = v[k0 + p] / A[(k0 + p) + int64_t(n) * (k0 + p)];
-        __syncwarp();
-        if (tid == p) v[k0 + p] = zp;
-        if (tid > p && tid < kb) v[k0 + tid] = fmaf(-A[(k0 + tid) + int64_t(n) * (k0 + p)], zp, v[k0 + tid]);
+        const float zp = __shfl_sync(0xffffffffu, vi, p) / sh.blk[p + L * p];
+        if (tid == p) vi = zp;
+        else if (tid > p && tid < kb) vi = fmaf(-sh.blk[tid + L * p], zp, vi);
       }
+      if (tid < kb) v[k0 + tid] = vi;
     }
     __syncthreads();
     for (int r = k0 + kb + tid; r < n; r += BT) {
@@ -468,14 +490,19 @@ __device__ void b_tri_solve(const BCtx& c, BShared<TF>& sh) {
   for (int k0 = last; k0 >= 0; k0 -= BNB) {     // backward: L^T y = z
     const int kb = (n - k0) < BNB ? (n - k0) : BNB;
     __syncthreads();
+    for (int e = tid; e < kb * kb; e += BT) {
+      const int i = e % kb, j = e / kb;
+      if (i >= j) sh.blk[i + L * j] = A[(k0 + i) + int64_t(n) * (k0 + j)];
+    }
+    __syncthreads();
     if (tid < 32) {
+      float vi = (tid < kb) ? v[k0 + tid] : 0.f;
       for (int p = kb - 1; p >= 0; --p) {
-        __syncwarp();
-        const float yp = v[k0 + p] / A[(k0 + p) + int64_t(n) * (k0 + p)];
-        __syncwarp();
-        if (tid == p) v[k0 + p] = yp;
-        if (tid < p) v[k0 + tid] = fmaf(-A[(k0 + p) + int64_t(n) * (k0 + tid)], yp, v[k0 + tid]);
+        const float yp = __shfl_sync(0xffffffffu, vi, p) / sh.blk[p + L * p];
+        if (tid == p) vi = yp;
+        else if (tid < p) vi = fmaf(-sh.blk[p + L * tid], yp, vi);
       }
+      if (tid < kb) v[k0 + tid] = vi;
     }
     __syncthreads();
     for (int r = tid; r < k0; r += BT) {

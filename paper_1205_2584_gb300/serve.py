@@ -251,7 +251,8 @@ class _Lane:
         self.trials = trials
         self.tile = tile
         dev = server.device
-        self.stream = torch.cuda.Stream(device=dev)
+        # lanes hold many short requests: their rounds go first when SMs free up
+        self.stream = torch.cuda.Stream(device=dev, priority=-1)
         self.ws_base = idx * _ALIGN                 # this lane's queue counter
         self.desc = (cp.BatchProblem * slots)()
         for s in range(slots):
