@@ -71,7 +71,7 @@ enum cp_code {
 /* core-system solver of cp_dgn_solve / cp_dgn_step */
 enum cp_core_mode {
   CP_CORE_F64 = 0,    /* float64 Cholesky of the core system */
-  CP_CORE_MIXED = 1   /* float32 Cholesky + float64 iterative refinement */
+  CP_CORE_MIXED = 1   /* float32 Gauss-Jordan inverse + float64 iterative refinement */
 };
 
 /* stop reasons in cp_status.stop */
@@ -122,7 +122,8 @@ typedef struct cp_status {
   int32_t error;           /* enum cp_code of the first device-side error */
   int32_t last_accepted;   /* 1 if the last trial was accepted */
   int32_t info;            /* first non-positive pivot (1-based) of the last factorisation */
-  int32_t reserved_i[2];
+  int32_t refine_sweeps;   /* refinement residuals formed by the last CP_CORE_MIXED solve */
+  int32_t reserved_i[1];
 } cp_status;
 
 typedef struct cp_state cp_state;   /* opaque host handle */

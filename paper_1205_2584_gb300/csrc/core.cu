@@ -226,10 +226,11 @@ template int launch_core_fill<float>(const Dims&, const double*, const double*, 
 // ---------------------------------------------------------------------------
 constexpr int kOpThreads = 128;
 
-// V = (K x)_n into shared memory: V[i + R j] = sum_{m != n} Gamma^(n,m)[i,j] X_m[j,i]
-__device__ void stage_Kx(const Dims& d, int n, const double* Gnm, const double* x, double* V) {
+// Columns 0..jmax of V = (K x)_n into shared memory:
+// V[i + R j] = sum_{m != n} Gamma^(n,m)[i,j] X_m[j,i]
+__device__ void stage_Kx(const Dims& d, int n, int jmax, const double* Gnm, const double* x, double* V) {
   const int R = d.R, RR = d.RR, N = d.N;
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+  for (int e = threadIdx.x; e < R * (jmax + 1); e += blockDim.x) {
     const int i = e % R, j = e / R;
     double s = 0.0;
     for (int m = 0; m < N; ++m)
@@ -253,64 +254,86 @@ __global__ void k_apply_K(Dims d, const double* Gnm, const double* x, const doub
   out[idx] = base ? base[idx] - s : s;
 }
 
+// The two small products of a column of S x / S^T x are float64 dot products
+// of length <= R.  Each is split over the CTA's four warps (thread (w, p)
+// takes every fourth term, starting at w) so that all four sub-partitions of
+// the SM feed its float64 pipe; the four partial sums are then added in a
+// fixed order.
+constexpr int kOpWarps = kOpThreads / 32;
+static_assert(kOpWarps == 4, "the partial sums below are added as four terms");
+
 // out_m = vec(L_m X_m U_m^T): CTA (m, q) computes column q.
 __global__ void __launch_bounds__(kOpThreads) k_apply_S(Dims d, const double* LC, const double* U,
                                                         const double* x, double* out, const int* skip) {
   if (skip && *skip) return;
   __shared__ double X[kRR], L[kRR], uq[CP_MAX_R], t[CP_MAX_R];
+  __shared__ double part[2][kOpWarps][CP_MAX_R];
   const int R = d.R, RR = d.RR;
   const int m = blockIdx.x / R, q = blockIdx.x % R;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, w = tid / 32, p = tid % 32;
   for (int e = tid; e < RR; e += kOpThreads) {
     X[e] = x[int64_t(m) * RR + e];
     L[e] = LC[int64_t(m) * RR + e];
   }
   if (tid < R) uq[tid] = U[int64_t(m) * RR + q + R * tid];   // row q of U_m
   __syncthreads();
-  if (tid < R) {   // t = X U_m[q, :]^T ; U_m upper: U_m[q,l] = 0 for l < q
+  if (p < R) {   // t = X U_m[q, :]^T ; U_m upper: U_m[q,l] = 0 for l < q
     double s = 0.0;
-    for (int l = q; l < R; ++l) s = fma(X[tid + R * l], uq[l], s);
-    t[tid] = s;
+    for (int l = q + w; l < R; l += kOpWarps) s = fma(X[p + R * l], uq[l], s);
+    part[0][w][p] = s;
   }
   __syncthreads();
-  if (tid < R) {   // out[:, q] = L_m t ; L_m[p,k] = 0 for k > p
+  if (tid < R) t[tid] = (part[0][0][tid] + part[0][1][tid]) + (part[0][2][tid] + part[0][3][tid]);
+  __syncthreads();
+  if (p < R) {   // out[:, q] = L_m t ; L_m[p,k] = 0 for k > p
     double s = 0.0;
-    for (int k = 0; k <= tid; ++k) s = fma(L[tid + R * k], t[k], s);
-    out[int64_t(m) * RR + tid + R * q] = s;
+    for (int k = w; k <= p; k += kOpWarps) s = fma(L[p + R * k], t[k], s);
+    part[1][w][p] = s;
   }
+  __syncthreads();
+  if (tid < R)
+    out[int64_t(m) * RR + tid + R * q] = (part[1][0][tid] + part[1][1][tid]) + (part[1][2][tid] + part[1][3][tid]);
 }
 
 // out_n = vec(L_n^T V_n U_n) with V_n = x_n (kx = 0) or V_n = (K x)_n (kx = 1).
 // b != null: out = b - y - (that)  (refinement residual b - y - S^T K S y).
-// kw != null (kx = 1): CTA q == 0 also stores V_n = (K x)_n into kw.
+// kw != null (kx = 1): CTA q also stores column q of V_n = (K x)_n into kw.
+// Column q needs columns 0..q of V_n only (U_n is upper triangular).
 __global__ void __launch_bounds__(kOpThreads) k_apply_ST(Dims d, const double* LC, const double* U,
                                                          const double* Gnm, const double* x, int kx,
                                                          const double* b, const double* y, double* out,
                                                          double* kw, double* norm2, const int* skip) {
   if (skip && *skip) return;
   __shared__ double V[kRR], L[kRR], uq[CP_MAX_R], t[CP_MAX_R];
+  __shared__ double part[2][kOpWarps][CP_MAX_R];
   const int R = d.R, RR = d.RR;
   const int n = blockIdx.x / R, q = blockIdx.x % R;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, w = tid / 32, p = tid % 32;
   if (kx) {
-    stage_Kx(d, n, Gnm, x, V);
+    stage_Kx(d, n, q, Gnm, x, V);
   } else {
-    for (int e = tid; e < RR; e += kOpThreads) V[e] = x[int64_t(n) * RR + e];
+    for (int e = tid; e < R * (q + 1); e += kOpThreads) V[e] = x[int64_t(n) * RR + e];
   }
   for (int e = tid; e < RR; e += kOpThreads) L[e] = LC[int64_t(n) * RR + e];
   if (tid < R) uq[tid] = U[int64_t(n) * RR + tid + R * q];   // column q of U_n
   __syncthreads();
-  if (kw && q == 0)
-    for (int e = tid; e < RR; e += kOpThreads) kw[int64_t(n) * RR + e] = V[e];
-  if (tid < R) {   // t = V U_n[:, q] ; U_n[l,q] = 0 for l > q
+  if (kw && tid < R) kw[int64_t(n) * RR + tid + R * q] = V[tid + R * q];
+  if (p < R) {   // t = V U_n[:, q] ; U_n[l,q] = 0 for l > q
     double s = 0.0;
-    for (int l = 0; l <= q; ++l) s = fma(V[tid + R * l], uq[l], s);
-    t[tid] = s;
+    for (int l = w; l <= q; l += kOpWarps) s = fma(V[p + R * l], uq[l], s);
+    part[0][w][p] = s;
   }
   __syncthreads();
-  if (tid < R) {   // out[:, q] = L_n^T t ; L_n[k,p] = 0 for k < p
+  if (tid < R) t[tid] = (part[0][0][tid] + part[0][1][tid]) + (part[0][2][tid] + part[0][3][tid]);
+  __syncthreads();
+  if (p < R) {   // out[:, q] = L_n^T t ; L_n[k,p] = 0 for k < p
     double s = 0.0;
-    for (int k = tid; k < R; ++k) s = fma(L[k + R * tid], t[k], s);
+    for (int k = p + w; k < R; k += kOpWarps) s = fma(L[k + R * p], t[k], s);
+    part[1][w][p] = s;
+  }
+  __syncthreads();
+  if (tid < R) {
+    const double s = (part[1][0][tid] + part[1][1][tid]) + (part[1][2][tid] + part[1][3][tid]);
     const int64_t o = int64_t(n) * RR + tid + R * q;
     const double val = b ? (b[o] - y[o] - s) : s;
     out[o] = val;

@@ -234,12 +234,15 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
     st->info = bad;
     {
       double rr = 0.0;   // relative residual of the last refinement sweep that ran
+      int sweeps = 0;
       for (int k = kMaxRefine; k >= 1; --k)
         if (scal[SC_NRM + k] > 0.0) {
           rr = sqrt(scal[SC_NRM + k] / scal[SC_NRM]);
+          sweeps = k;
           break;
         }
       st->refine_resid = rr;
+      st->refine_sweeps = sweeps;
     }
     st->mu = mu;
     st->nu = nu;
@@ -330,7 +333,8 @@ __global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double
   s.error = 0;
   s.last_accepted = 0;
   s.info = 0;
-  s.reserved_i[0] = s.reserved_i[1] = 0;
+  s.refine_sweeps = 0;
+  s.reserved_i[0] = 0;
   *st = s;
   *mu_copy = s.mu;
 }

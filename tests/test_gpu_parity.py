@@ -252,3 +252,4 @@ def test_full_size_config3_sampled(cp):
     trial = [a0 + d.numpy() for a0, d in zip(p.init, delta)]
     assert st.status()["resid2_trial"] == pytest.approx(O.residual2(p.Y, trial), rel=1e-5)
     assert st.status()["refine_resid"] < 1e-8
+    assert 1 <= st.status()["refine_sweeps"] <= 8
