@@ -237,6 +237,26 @@ def oracle_rate(problem, seconds: float):
     return res.iters / dt, res.iters, dt
 
 
+def oracle_rate_one_thread(seed: int, seconds: float):
+    """oracle_rate on one host thread: a child interpreter with the BLAS and
+    OpenMP pools limited to one thread before numpy loads."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "from paper_1205_2584_gb300 import synth; "
+            "p = synth.config2(%d, bench.DIMS, dtype='bf16x2'); "
+            "print(json.dumps(bench.oracle_rate(p, %f)))") % (ROOT, seed, seconds)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=max(120.0, 10 * seconds))
+        rate, iters, secs = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": rate, "unit": "iters/s", "cores": 1,
+                "sample": f"first {iters} LM iterations, {secs:.1f} s"}
+    except Exception as e:   # reported, never fatal
+        return {"value": None, "error": str(e)[:200]}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -469,7 +489,8 @@ def _run_ours(args, rank, world, local):
         out["cpu_baseline"] = {"value": rate, "unit": "iters/s", "cores": oracle_threads(),
                                "kind": "oracle",
                                "sample": f"first {iters} LM iterations of the same 200^3 R=20 problem "
-                                         f"(the same tensor values in float64), {secs:.1f} s"}
+                                         f"(the same tensor values in float64), {secs:.1f} s",
+                               "one_thread": oracle_rate_one_thread(seed, max(2.0, args.cpu_seconds / 3))}
     st.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -8,101 +8,128 @@
 //     B[i,k] = -A[i,k] P^{-1}               (i != k)      k_gj_update
 //     B[i,j] = A[i,j] - A[i,k] B[k,j]       (i, j != k)   k_gj_update
 // and after the last panel B = A^{-1}.  No pivoting is needed for an SPD
-// matrix (each pivot block is a Schur complement of an SPD matrix).  P^{-1}
-// of sweep k + 1 is computed during sweep k by one CTA (k_gj_pivot_next) on a
-// side stream.  A and B alternate between sweeps.  A non-positive or
-// non-finite pivot sets *info (1-based row); nothing traps.
+// matrix (each pivot block is a Schur complement of an SPD matrix).  A and B
+// alternate between sweeps.  A non-positive or non-finite pivot sets *info
+// (1-based row); nothing traps.
 //
-// Every tile kernel runs 256 threads on a 64 x 64 tile; thread (bi, bj) owns
-// rows 4 bi .. 4 bi + 3 and columns 4 bj .. 4 bj + 3, so each k-step of a
-// tile product reads one float4 of the left operand (stored column by column,
-// rows contiguous) and one float4 of the right operand (stored row by row)
-// for 16 multiply-adds.
+// The sequential part is the chain of pivot inverses.  P^{-1} of sweep k + 1
+// is formed and inverted during sweep k by one CTA (k_gj_pivot_next) on a side
+// stream, from sweep k's input alone, so it overlaps sweep k's row panel and
+// update.  That CTA reserves nearly all of its SM's shared memory, so no tile
+// CTA shares the SM with it.
+//
+// Tile products: thread (bi, bj) owns rows 4 bi .. 4 bi + 3 and columns
+// 4 bj .. 4 bj + 3 of a 64 x TC output tile (TC = 64: 256 threads; TC = 32:
+// 128 threads), so each k-step reads one float4 of the left operand (stored
+// column by column, rows contiguous) and one float4 of the right operand
+// (stored row by row) for 16 multiply-adds.  The row panel and the update
+// work on 64 x 32 half tiles: twice as many CTAs as tiles, which spreads a
+// sweep evenly over the SMs.
 #include "common.cuh"
 
 namespace cpdgn {
 
-constexpr int GJB = 64;           // panel / tile width
-constexpr int GJT = 256;          // threads per CTA: 16 x 16 threads, 4 x 4 entries each
+constexpr int GJB = 64;           // panel / tile height
+constexpr int GJT = 256;          // threads of a 64 x 64 tile CTA: 16 x 16 threads, 4 x 4 entries each
+constexpr int GJH = 32;           // width of a half tile
+constexpr int GJTH = 128;         // threads of a 64 x 32 half-tile CTA
 constexpr int GJP = GJB + 4;      // padded row length in shared memory (keeps float4 alignment)
+// shared memory reserved by k_gj_pivot_next on top of its static arrays
+// (about 53 KB): with it the CTA holds about 221 KB of the SM's 228 KB, so no
+// half-tile CTA (about 27 KB) fits beside it; the sum stays under the 227 KB
+// per-block limit
+constexpr int kPivotReserve = 168 * 1024;
 
 // Reciprocal of a pivot.  The float32 inverse only preconditions the float64
 // refinement, so the fast intrinsic division (about 2 ulp) is accurate enough.
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 
-// S[c][r] = A(64 ti + r, 64 tj + c) (zero outside n x n): columns of the tile,
-// rows contiguous.  Global reads are coalesced along r.
-__device__ __forceinline__ void load_cols(const float* A, int64_t n, int ti, int tj, float (*S)[GJP]) {
+// S[c][r] = sgn * A(r0 + r, c0 + c) for r, c < 64 (zero outside n x n): a
+// 64 x 64 left operand stored column by column.  Global reads are coalesced
+// along r.  NT threads.
+template <int NT>
+__device__ __forceinline__ void load_cols(const float* A, int64_t n, int64_t r0, int64_t c0, float (*S)[GJP],
+                                          float sgn) {
 #pragma unroll
-  for (int q = 0; q < GJB * GJB / GJT; ++q) {
-    const int e = int(threadIdx.x) + q * GJT;
+  for (int q = 0; q < GJB * GJB / NT; ++q) {
+    const int e = int(threadIdx.x) + q * NT;
     const int r = e % GJB, c = e / GJB;
-    const int64_t gr = int64_t(ti) * GJB + r, gc = int64_t(tj) * GJB + c;
-    S[c][r] = (gr < n && gc < n) ? A[gr + n * gc] : 0.f;
+    const int64_t gr = r0 + r, gc = c0 + c;
+    S[c][r] = (gr < n && gc < n) ? sgn * A[gr + n * gc] : 0.f;
   }
 }
 
-// S[r][c] = A(64 ti + r, 64 tj + c): rows of the tile, columns contiguous.
-__device__ __forceinline__ void load_rows(const float* A, int64_t n, int ti, int tj, float (*S)[GJP]) {
+// S[r][c] = A(r0 + r, c0 + c) for r < 64, c < TC: a right operand stored row
+// by row.  4 TC threads.
+template <int TC>
+__device__ __forceinline__ void load_rows(const float* A, int64_t n, int64_t r0, int64_t c0, float (*S)[TC + 4]) {
 #pragma unroll
-  for (int q = 0; q < GJB * GJB / GJT; ++q) {
-    const int e = int(threadIdx.x) + q * GJT;
+  for (int q = 0; q < GJB / 4; ++q) {
+    const int e = int(threadIdx.x) + q * 4 * TC;
     const int r = e % GJB, c = e / GJB;
-    const int64_t gr = int64_t(ti) * GJB + r, gc = int64_t(tj) * GJB + c;
+    const int64_t gr = r0 + r, gc = c0 + c;
     S[r][c] = (gr < n && gc < n) ? A[gr + n * gc] : 0.f;
   }
 }
 
-// the thread's 4 x 4 block of tile (ti, tj); rows beyond n read as 0
-__device__ __forceinline__ void load_block(const float* A, int64_t n, int ti, int tj, float (&x)[4][4]) {
+// the thread's 4 x 4 block of the 64 x TC tile at (r0, c0); entries outside n x n read as 0
+__device__ __forceinline__ void load_block(const float* A, int64_t n, int64_t r0, int64_t c0, float (&x)[4][4]) {
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
-  const int64_t r0 = int64_t(ti) * GJB + 4 * bi;
-  const bool vec = (n % 4 == 0) && (r0 + 3 < n);
+  const int64_t rr = r0 + 4 * bi;
+  const bool vec = (n % 4 == 0) && (rr + 3 < n);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const int64_t c = int64_t(tj) * GJB + 4 * bj + v;
+    const int64_t c = c0 + 4 * bj + v;
     if (c >= n) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) x[u][v] = 0.f;
     } else if (vec) {
-      const float4 t = *reinterpret_cast<const float4*>(A + r0 + n * c);
+      const float4 t = *reinterpret_cast<const float4*>(A + rr + n * c);
       x[0][v] = t.x;
       x[1][v] = t.y;
       x[2][v] = t.z;
       x[3][v] = t.w;
     } else {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) x[u][v] = (r0 + u < n) ? A[r0 + u + n * c] : 0.f;
+      for (int u = 0; u < 4; ++u) x[u][v] = (rr + u < n) ? A[rr + u + n * c] : 0.f;
     }
   }
 }
 
-__device__ __forceinline__ void store_block(const float (&x)[4][4], float* B, int64_t n, int ti, int tj) {
+__device__ __forceinline__ void store_block(const float (&x)[4][4], float* B, int64_t n, int64_t r0, int64_t c0) {
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
-  const int64_t r0 = int64_t(ti) * GJB + 4 * bi;
-  const bool vec = (n % 4 == 0) && (r0 + 3 < n);
+  const int64_t rr = r0 + 4 * bi;
+  const bool vec = (n % 4 == 0) && (rr + 3 < n);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const int64_t c = int64_t(tj) * GJB + 4 * bj + v;
+    const int64_t c = c0 + 4 * bj + v;
     if (c >= n) continue;
     if (vec) {
-      *reinterpret_cast<float4*>(B + r0 + n * c) = make_float4(x[0][v], x[1][v], x[2][v], x[3][v]);
+      *reinterpret_cast<float4*>(B + rr + n * c) = make_float4(x[0][v], x[1][v], x[2][v], x[3][v]);
     } else {
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (r0 + u < n) B[r0 + u + n * c] = x[u][v];
+        if (rr + u < n) B[rr + u + n * c] = x[u][v];
     }
   }
 }
 
-// x (+)= sgn * L R with L = Lc (columns, rows contiguous) and R = Rr (rows).
-__device__ __forceinline__ void tile_fma(const float (*Lc)[GJP], const float (*Rr)[GJP], float sgn, float (&x)[4][4]) {
+__device__ __forceinline__ void zero_block(float (&x)[4][4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) x[u][v] = 0.f;
+}
+
+// x += L R with L = Lc (64 x 64, columns) and R = Rr (64 x TC, rows).
+template <int TC>
+__device__ __forceinline__ void tile_fma(const float (*Lc)[GJP], const float (*Rr)[TC + 4], float (&x)[4][4]) {
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
 #pragma unroll 8
   for (int l = 0; l < GJB; ++l) {
     const float4 a = *reinterpret_cast<const float4*>(&Lc[l][4 * bi]);
     const float4 b = *reinterpret_cast<const float4*>(&Rr[l][4 * bj]);
-    const float av[4] = {sgn * a.x, sgn * a.y, sgn * a.z, sgn * a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -110,54 +137,52 @@ __device__ __forceinline__ void tile_fma(const float (*Lc)[GJP], const float (*R
   }
 }
 
-// Row panel: B[k,j] = P^{-1} A[k,j] for j != k; CTA = tile column j.
+// Row panel: B[k,j] = P^{-1} A[k,j] for j != k; CTA = one half tile of row k.
 template <typename T>
-__global__ void __launch_bounds__(GJT) k_gj_rowpanel(const T* A, T* B, int64_t n, int k, const T* Pinv,
-                                                     const int* skip) {
+__global__ void __launch_bounds__(GJTH) k_gj_rowpanel(const T* A, T* B, int64_t n, int k, const T* Pinv,
+                                                      const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ps[GJB][GJP], Xs[GJB][GJP];
+  __shared__ __align__(16) float Ps[GJB][GJP], Xs[GJB][GJH + 4];
   const int nt = int((n + GJB - 1) / GJB);
-  const int tj = blockIdx.x >= k ? blockIdx.x + 1 : blockIdx.x;
-  if (tj >= nt) return;
-  load_cols(Pinv, GJB, 0, 0, Ps);
-  load_rows(A, n, k, tj, Xs);
+  const int jj = int(blockIdx.x) / 2, h = int(blockIdx.x) % 2;
+  const int tj = jj >= k ? jj + 1 : jj;
+  const int64_t c0 = int64_t(tj) * GJB + h * GJH;
+  if (tj >= nt || c0 >= n) return;
+  load_cols<GJTH>(Pinv, GJB, 0, 0, Ps, 1.f);
+  load_rows<GJH>(A, n, int64_t(k) * GJB, c0, Xs);
   float acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  zero_block(acc);
   __syncthreads();
-  tile_fma(Ps, Xs, 1.f, acc);
-  store_block(acc, B, n, k, tj);
+  tile_fma<GJH>(Ps, Xs, acc);
+  store_block(acc, B, n, int64_t(k) * GJB, c0);
 }
 
-// Update of every tile outside row k.  When skip_pivot is set, tile
+// Update of every half tile outside row k.  When skip_pivot is set, tile
 // (k+1, k+1) is left to k_gj_pivot_next (which runs concurrently).
 template <typename T>
-__global__ void __launch_bounds__(GJT) k_gj_update(const T* A, T* B, int64_t n, int k, const T* Pinv,
-                                                   int skip_pivot, const int* skip) {
+__global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n, int k, const T* Pinv,
+                                                    int skip_pivot, const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP];
+  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJH + 4];
   const int nt = int((n + GJB - 1) / GJB);
-  const int b = int(blockIdx.x);
+  const int h = int(blockIdx.x) % 2, b = int(blockIdx.x) / 2;
   const int ti = b % (nt - 1) >= k ? b % (nt - 1) + 1 : b % (nt - 1);
   const int tj = b / (nt - 1);
   if (skip_pivot && ti == k + 1 && tj == k + 1) return;
-  load_cols(A, n, ti, k, Ls);                        // A[i,k]
-  if (tj == k) load_rows(Pinv, GJB, 0, 0, Rs);
-  else load_rows(B, n, k, tj, Rs);                   // B[k,j] from the row panel
+  const int64_t r0 = int64_t(ti) * GJB, c0 = int64_t(tj) * GJB + h * GJH;
+  if (c0 >= n) return;
+  load_cols<GJTH>(A, n, r0, int64_t(k) * GJB, Ls, -1.f);   // -A[i,k]
   float acc[4][4];
   if (tj == k) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    load_rows<GJH>(Pinv, GJB, 0, h * GJH, Rs);
+    zero_block(acc);
   } else {
-    load_block(A, n, ti, tj, acc);
+    load_rows<GJH>(B, n, int64_t(k) * GJB, c0, Rs);         // B[k,j] from the row panel
+    load_block(A, n, r0, c0, acc);
   }
   __syncthreads();
-  tile_fma(Ls, Rs, -1.f, acc);
-  store_block(acc, B, n, ti, tj);
+  tile_fma<GJH>(Ls, Rs, acc);
+  store_block(acc, B, n, r0, c0);
 }
 
 // The first kb0 tiles of the core lie inside its leading identity block
@@ -173,16 +198,16 @@ __global__ void __launch_bounds__(GJT) k_gj_identity(const T* A, T* B, int64_t n
   const int nt = int((n + GJB - 1) / GJB);
   const int ti = blockIdx.x % nt, tj = blockIdx.x / nt;
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+  const int64_t r0 = int64_t(ti) * GJB, c0 = int64_t(tj) * GJB;
   float acc[4][4];
   if (ti < kb0 || tj < kb0) {
     if (ti < kb0 && tj < kb0) {
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          acc[u][v] = (int64_t(ti) * GJB + 4 * bi + u == int64_t(tj) * GJB + 4 * bj + v) ? 1.f : 0.f;
+        for (int v = 0; v < 4; ++v) acc[u][v] = (r0 + 4 * bi + u == c0 + 4 * bj + v) ? 1.f : 0.f;
     } else {
-      load_block(A, n, ti, tj, acc);
+      load_block(A, n, r0, c0, acc);
       if (ti >= kb0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -190,18 +215,18 @@ __global__ void __launch_bounds__(GJT) k_gj_identity(const T* A, T* B, int64_t n
           for (int v = 0; v < 4; ++v) acc[u][v] = -acc[u][v];
       }
     }
-    store_block(acc, B, n, ti, tj);
+    store_block(acc, B, n, r0, c0);
     return;
   }
-  load_block(A, n, ti, tj, acc);
+  load_block(A, n, r0, c0, acc);
   for (int kk = 0; kk < kb0; ++kk) {
     __syncthreads();
-    load_cols(A, n, ti, kk, Ls);
-    load_rows(A, n, kk, tj, Rs);
+    load_cols<GJT>(A, n, r0, int64_t(kk) * GJB, Ls, -1.f);
+    load_rows<GJB>(A, n, int64_t(kk) * GJB, c0, Rs);
     __syncthreads();
-    tile_fma(Ls, Rs, -1.f, acc);
+    tile_fma<GJB>(Ls, Rs, acc);
   }
-  store_block(acc, B, n, ti, tj);
+  store_block(acc, B, n, r0, c0);
 }
 
 // ---------------------------------------------------------------------------
@@ -292,7 +317,7 @@ __device__ void pivot_store(float (&x)[4][4], int64_t n, int kk, int kb, float* 
   gj_invert_tile(x, kb, prow, pcol, bad);
   if (threadIdx.x == 0 && *bad <= GJB && info) atomicCAS(info, 0, kk * GJB + *bad);
   store_block(x, Pinv, GJB, 0, 0);
-  store_block(x, D, n, kk, kk);
+  store_block(x, D, n, int64_t(kk) * GJB, int64_t(kk) * GJB);
 }
 
 // Pivot of sweep k (tile (k, k) of A as it stands); P^{-1} also into D's tile.
@@ -304,29 +329,43 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot(const T* A, T* D, int64_t n, i
   __shared__ int bad;
   const int kb = int((n - int64_t(k) * GJB) < GJB ? (n - int64_t(k) * GJB) : GJB);
   float x[4][4];
-  load_block(A, n, k, k, x);
+  load_block(A, n, int64_t(k) * GJB, int64_t(k) * GJB, x);
   pad_identity(x, kb);
   pivot_store(x, n, k, kb, Pinv, D, info, prow, pcol, &bad);
 }
 
-// Pivot of sweep k + 1 during sweep k: X = A[k+1,k+1] - A[k+1,k] B[k,k+1],
-// inverted; P^{-1} goes to Pinv_next and into A's tile (k+1, k+1), which sweep
-// k + 1 writes into and which nobody else reads during sweep k.
+// Pivot of sweep k + 1 during sweep k, from sweep k's input A and pivot
+// inverse Pinv alone: X = A[k+1,k+1] - A[k+1,k] (P^{-1} A[k,k+1]), inverted;
+// X^{-1} goes to Pinv_next and into A's tile (k+1, k+1), which sweep k + 1
+// writes into and which no kernel of sweep k reads.  All three tiles of A are
+// fetched before the first product.  Launched with kPivotReserve bytes of
+// dynamic shared memory (unused: it keeps the tile CTAs of the concurrent
+// sweep off this SM).
 template <typename T>
-__global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, const T* B, int64_t n, int k, T* Pinv_next,
+__global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, const T* Pinv, T* Pinv_next,
                                                        int* info, const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP];
+  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP], L2s[GJB][GJP];
   __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
   __shared__ int bad;
   const int k1 = k + 1;
   const int kb = int((n - int64_t(k1) * GJB) < GJB ? (n - int64_t(k1) * GJB) : GJB);
-  load_cols(A, n, k1, k, Ls);          // A[k+1, k]
-  load_rows(B, n, k, k1, Rs);          // B[k, k+1]
-  float x[4][4];
-  load_block(A, n, k1, k1, x);
+  const int64_t o = int64_t(k) * GJB, o1 = int64_t(k1) * GJB;
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+  load_cols<GJT>(Pinv, GJB, 0, 0, Ls, 1.f);
+  load_rows<GJB>(A, n, o, o1, Rs);                   // A[k, k+1]
+  load_cols<GJT>(A, n, o1, o, L2s, -1.f);            // -A[k+1, k]
+  float x[4][4], t[4][4];
+  load_block(A, n, o1, o1, x);                       // A[k+1, k+1]
+  zero_block(t);
   __syncthreads();
-  tile_fma(Ls, Rs, -1.f, x);
+  tile_fma<GJB>(Ls, Rs, t);                          // t = P^{-1} A[k, k+1]
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    *reinterpret_cast<float4*>(&Rs[4 * bi + u][4 * bj]) = make_float4(t[u][0], t[u][1], t[u][2], t[u][3]);
+  __syncthreads();
+  tile_fma<GJB>(L2s, Rs, x);
   pad_identity(x, kb);
   pivot_store(x, n, k1, kb, Pinv_next, A, info, prow, pcol, &bad);
 }
@@ -336,10 +375,14 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, const T* B, int64_t
 // the inverse.  When the leading `ident` rows/columns of A are the identity,
 // the first ident / GJB sweeps are replaced by one block elimination.  With
 // side != null the pivot of sweep k + 1 is inverted on `side` while sweep k's
-// update runs on s (fork/join through ev_fork / ev_join, graph-capturable).
+// row panel and update run on s (fork/join through ev_fork / ev_join,
+// graph-capturable).
 template <typename T>
 int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const int* skip, cudaStream_t s,
               cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result) {
+  if (side && cudaFuncSetAttribute(k_gj_pivot_next<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kPivotReserve) != cudaSuccess)
+    return CP_ECUDA;
   const int nt = int((n + GJB - 1) / GJB);
   T* src = A;
   T* dst = B;
@@ -356,15 +399,15 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
     T* pk = pinv + size_t(k & 1) * GJB * GJB;
     T* pn = pinv + size_t((k + 1) & 1) * GJB * GJB;
     if (nt > 1) {
-      k_gj_rowpanel<T><<<nt - 1, GJT, 0, s>>>(src, dst, n, k, pk, skip);
       const bool next = (k + 1 < nt);
       if (next && side) {
         if (cudaEventRecord(ev_fork, s) != cudaSuccess) return CP_ECUDA;
         if (cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return CP_ECUDA;
-        k_gj_pivot_next<T><<<1, GJT, 0, side>>>(src, dst, n, k, pn, info, skip);
+        k_gj_pivot_next<T><<<1, GJT, kPivotReserve, side>>>(src, n, k, pk, pn, info, skip);
         if (cudaEventRecord(ev_join, side) != cudaSuccess) return CP_ECUDA;
       }
-      k_gj_update<T><<<(nt - 1) * nt, GJT, 0, s>>>(src, dst, n, k, pk, (next && side) ? 1 : 0, skip);
+      k_gj_rowpanel<T><<<(nt - 1) * 2, GJTH, 0, s>>>(src, dst, n, k, pk, skip);
+      k_gj_update<T><<<(nt - 1) * nt * 2, GJTH, 0, s>>>(src, dst, n, k, pk, (next && side) ? 1 : 0, skip);
       if (next && side) {
         if (cudaStreamWaitEvent(s, ev_join, 0) != cudaSuccess) return CP_ECUDA;
       } else if (next) {
