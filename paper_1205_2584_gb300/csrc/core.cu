@@ -31,6 +31,8 @@ namespace cpdgn {
 constexpr int kRR = CP_MAX_R * CP_MAX_R;
 
 constexpr int kPrepThreads = 128;
+constexpr int kPrepWarps = kPrepThreads / 32;
+static_assert(kPrepWarps == 4, "the partial sums of k_mode_prep are added as four terms");
 
 // CTA (n, j), j < R: column j of Gt^(n), U_n and w_n.
 //   Gt[:, j] = L_G^{-T} L_G^{-1} e_j;  U[:, j] = L_G^{-T} e_j
@@ -44,19 +46,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
   if (skip && *skip) return;
   __shared__ double G[kRR], Gam[kRR], Cn[kRR], Pn[kRR];
   __shared__ double z[CP_MAX_R], u[CP_MAX_R], v[CP_MAX_R], rinv[CP_MAX_R];
+  __shared__ double part[2][kPrepWarps][CP_MAX_R];
   __shared__ int okc;
   const int R = d.R, RR = d.RR, N = d.N;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   if (int(blockIdx.x) >= N * R) {                 // Cholesky of C^(n)
     const int n = blockIdx.x - N * R;
     for (int e = tid; e < RR; e += kPrepThreads) G[e] = C[int64_t(n) * RR + e];
-    __syncthreads();
-    if (warp == 0) {
-      const bool ok = warp_chol(G, rinv, R);
-      if (lane == 0) okc = ok;
-    }
-    __syncthreads();
-    if (tid == 0 && info && !okc) atomicCAS(info, 0, n + 1);
+    const bool ok = cta_chol(G, rinv, R, &okc);
+    if (tid == 0 && info && !ok) atomicCAS(info, 0, n + 1);
     for (int e = tid; e < RR; e += kPrepThreads) {
       const int i = e % R, jj = e / R;
       LC[int64_t(n) * RR + e] = (i >= jj) ? G[e] : 0.0;
@@ -82,33 +80,42 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
       }
     }
   }
-  __syncthreads();
-  if (warp == 0) {
-    const bool okG = warp_chol(G, rinv, R);
-    if (lane == 0) okc = okG;
-  }
-  __syncthreads();
-  if (tid == 0 && j == 0 && info && !okc) atomicCAS(info, 0, n + 1);
+  const bool okG = cta_chol(G, rinv, R, &okc);
+  if (tid == 0 && j == 0 && info && !okG) atomicCAS(info, 0, n + 1);
   if (warp == 0) {
     if (lane < R) z[lane] = (lane == j) ? 1.0 : 0.0;
     warp_fwd(G, rinv, z, R);
     warp_bwd(G, rinv, z, R);   // z = Gt e_j
   } else if (warp == 1) {
     if (lane < R) u[lane] = (lane == j) ? 1.0 : 0.0;
+    warp_bwd(G, rinv, u, R);   // u = L_G^{-T} e_j, concurrently with z
   }
   __syncthreads();
-  if (warp == 1) warp_bwd(G, rinv, u, R);   // u = L_G^{-T} e_j (overlaps the products below)
-  if (tid < R) {
+  // the three length-R dot products per entry below are float64 chains of
+  // ~40-cycle dependent multiply-adds; each is split over the four warps
+  // (warp w takes every fourth term) and the partial sums added in order
+  if (lane < R) {
     double s = 0.0;
-    for (int c = 0; c < R; ++c) s = fma(Gam[tid + R * c], z[c], s);
-    v[tid] = s;
+    for (int c = warp; c < R; c += kPrepWarps) s = fma(Gam[lane + R * c], z[c], s);
+    part[0][warp][lane] = s;
+  }
+  __syncthreads();
+  if (tid < R) v[tid] = (part[0][0][tid] + part[0][1][tid]) + (part[0][2][tid] + part[0][3][tid]);
+  __syncthreads();
+  if (lane < R) {
+    double s = 0.0, t = 0.0;
+    for (int c = warp; c < R; c += kPrepWarps) {
+      s = fma(Pn[lane + R * c], z[c], s);
+      t = fma(Cn[lane + R * c], v[c], t);
+    }
+    part[0][warp][lane] = s;
+    part[1][warp][lane] = t;
   }
   __syncthreads();
   if (tid < R) {
     const int64_t o = int64_t(n) * RR + tid + int64_t(R) * j;
-    double s = 0.0, t = 0.0;
-    for (int c = 0; c < R; ++c) s = fma(Pn[tid + R * c], z[c], s);
-    for (int c = 0; c < R; ++c) t = fma(Cn[tid + R * c], v[c], t);
+    const double s = (part[0][0][tid] + part[0][1][tid]) + (part[0][2][tid] + part[0][3][tid]);
+    const double t = (part[1][0][tid] + part[1][1][tid]) + (part[1][2][tid] + part[1][3][tid]);
     Gt[o] = z[tid];
     U[o] = u[tid];
     if (w) w[o] = s - t;

@@ -18,13 +18,17 @@
 // update.  That CTA reserves nearly all of its SM's shared memory, so no tile
 // CTA shares the SM with it.
 //
-// Tile products: thread (bi, bj) owns rows 4 bi .. 4 bi + 3 and columns
-// 4 bj .. 4 bj + 3 of a 64 x TC output tile (TC = 64: 256 threads; TC = 32:
-// 128 threads), so each k-step reads one float4 of the left operand (stored
-// column by column, rows contiguous) and one float4 of the right operand
-// (stored row by row) for 16 multiply-adds.  The row panel and the update
-// work on 64 x 32 half tiles: twice as many CTAs as tiles, which spreads a
-// sweep evenly over the SMs.
+// Tile products.  The pivot kernels (256 threads on a 64 x 64 tile): thread
+// (bi, bj) owns rows 4 bi .. 4 bi + 3 and columns 4 bj .. 4 bj + 3, so each
+// k-step reads one float4 of the left operand (stored column by column, rows
+// contiguous) and one float4 of the right operand (stored row by row) for 16
+// multiply-adds.  The row panel, the update and the identity elimination work
+// on 64 x 32 half tiles (twice as many CTAs as tiles, which spreads a sweep
+// evenly over the SMs) with 64 threads: thread (bi, bj) owns rows
+// 4 bi .. 4 bi + 3 and 32 + 4 bi .. 32 + 4 bi + 3 and columns 4 bj .. 4 bj + 3,
+// so each k-step reads two float4 of the left operand and one of the right
+// operand for 32 multiply-adds; eight consecutive lanes read eight
+// consecutive float4, free of shared-memory bank conflicts.
 #include "common.cuh"
 
 namespace cpdgn {
@@ -32,7 +36,7 @@ namespace cpdgn {
 constexpr int GJB = 64;           // panel / tile height
 constexpr int GJT = 256;          // threads of a 64 x 64 tile CTA: 16 x 16 threads, 4 x 4 entries each
 constexpr int GJH = 32;           // width of a half tile
-constexpr int GJTH = 128;         // threads of a 64 x 32 half-tile CTA
+constexpr int GJTH = 64;          // threads of a 64 x 32 half-tile CTA: 8 x 8 threads, 8 x 4 entries each
 constexpr int GJP = GJB + 4;      // padded row length in shared memory (keeps float4 alignment)
 // shared memory reserved by k_gj_pivot_next on top of its static arrays
 // (about 53 KB): with it the CTA holds about 221 KB of the SM's 228 KB, so no
@@ -137,6 +141,136 @@ __device__ __forceinline__ void tile_fma(const float (*Lc)[GJP], const float (*R
   }
 }
 
+// ---- half-tile kernels (64 threads, 8 x 4 entries per thread) ----
+
+// Ls[l][r] = sgn * A(r0 + r, c0 + l) for r, l < 64 (zero outside n x n).
+// With n % 4 == 0 the reads are float4 along r (tile origins are multiples of
+// 64, so they are 16-byte aligned).
+__device__ __forceinline__ void h_load_left(const float* A, int64_t n, int64_t r0, int64_t c0, float (*Ls)[GJP],
+                                            float sgn) {
+  if (n % 4 == 0) {
+#pragma unroll 4
+    for (int q = 0; q < GJB * GJB / 4 / GJTH; ++q) {
+      const int e = int(threadIdx.x) + q * GJTH;
+      const int r = 4 * (e % 16), l = e / 16;
+      const int64_t gr = r0 + r, gc = c0 + l;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < n && gc < n) v = *reinterpret_cast<const float4*>(A + gr + n * gc);
+      *reinterpret_cast<float4*>(&Ls[l][r]) = make_float4(sgn * v.x, sgn * v.y, sgn * v.z, sgn * v.w);
+    }
+  } else {
+#pragma unroll 4
+    for (int q = 0; q < GJB * GJB / GJTH; ++q) {
+      const int e = int(threadIdx.x) + q * GJTH;
+      const int r = e % GJB, l = e / GJB;
+      const int64_t gr = r0 + r, gc = c0 + l;
+      Ls[l][r] = (gr < n && gc < n) ? sgn * A[gr + n * gc] : 0.f;
+    }
+  }
+}
+
+// Rs[l][c] = A(r0 + l, c0 + c) for l < 64, c < 32.  With n % 4 == 0 each
+// thread reads a float4 along l and scatters it over 4 rows (consecutive
+// lanes take consecutive columns: no bank conflicts).
+__device__ __forceinline__ void h_load_right(const float* A, int64_t n, int64_t r0, int64_t c0,
+                                             float (*Rs)[GJH + 4]) {
+  if (n % 4 == 0) {
+#pragma unroll 4
+    for (int q = 0; q < GJB * GJH / 4 / GJTH; ++q) {
+      const int e = int(threadIdx.x) + q * GJTH;
+      const int c = e % GJH, l = 4 * (e / GJH);
+      const int64_t gr = r0 + l, gc = c0 + c;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < n && gc < n) v = *reinterpret_cast<const float4*>(A + gr + n * gc);
+      Rs[l][c] = v.x;
+      Rs[l + 1][c] = v.y;
+      Rs[l + 2][c] = v.z;
+      Rs[l + 3][c] = v.w;
+    }
+  } else {
+#pragma unroll 4
+    for (int q = 0; q < GJB * GJH / GJTH; ++q) {
+      const int e = int(threadIdx.x) + q * GJTH;
+      const int c = e % GJH, l = e / GJH;
+      const int64_t gr = r0 + l, gc = c0 + c;
+      Rs[l][c] = (gr < n && gc < n) ? A[gr + n * gc] : 0.f;
+    }
+  }
+}
+
+// row of entry (u, .) of thread bi: u < 4 -> 4 bi + u, u >= 4 -> 32 + 4 bi + u - 4
+__device__ __forceinline__ int h_row(int bi, int hh) { return 4 * bi + 32 * hh; }
+
+__device__ __forceinline__ void h_load_block(const float* A, int64_t n, int64_t r0, int64_t c0, float (&x)[8][4]) {
+  const int bi = threadIdx.x % 8, bj = threadIdx.x / 8;
+  const bool vec = (n % 4 == 0);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int64_t c = c0 + 4 * bj + v;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int64_t r = r0 + h_row(bi, hh);
+      if (vec) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < n && r < n) t = *reinterpret_cast<const float4*>(A + r + n * c);
+        x[4 * hh][v] = t.x;
+        x[4 * hh + 1][v] = t.y;
+        x[4 * hh + 2][v] = t.z;
+        x[4 * hh + 3][v] = t.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[4 * hh + u][v] = (c < n && r + u < n) ? A[r + u + n * c] : 0.f;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void h_store_block(const float (&x)[8][4], float* B, int64_t n, int64_t r0, int64_t c0) {
+  const int bi = threadIdx.x % 8, bj = threadIdx.x / 8;
+  const bool vec = (n % 4 == 0);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int64_t c = c0 + 4 * bj + v;
+    if (c >= n) continue;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int64_t r = r0 + h_row(bi, hh);
+      if (vec) {
+        if (r < n)
+          *reinterpret_cast<float4*>(B + r + n * c) =
+              make_float4(x[4 * hh][v], x[4 * hh + 1][v], x[4 * hh + 2][v], x[4 * hh + 3][v]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (r + u < n) B[r + u + n * c] = x[4 * hh + u][v];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void h_zero(float (&x)[8][4]) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) x[u][v] = 0.f;
+}
+
+// x += L R with L = Ls (64 x 64, k-major) and R = Rs (64 x 32, k-major).
+__device__ __forceinline__ void h_fma(const float (*Ls)[GJP], const float (*Rs)[GJH + 4], float (&x)[8][4]) {
+  const int bi = threadIdx.x % 8, bj = threadIdx.x / 8;
+#pragma unroll 8
+  for (int l = 0; l < GJB; ++l) {
+    const float4 a0 = *reinterpret_cast<const float4*>(&Ls[l][4 * bi]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&Ls[l][32 + 4 * bi]);
+    const float4 b = *reinterpret_cast<const float4*>(&Rs[l][4 * bj]);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) x[u][v] = fmaf(av[u], bv[v], x[u][v]);
+  }
+}
+
 // Row panel: B[k,j] = P^{-1} A[k,j] for j != k; CTA = one half tile of row k.
 template <typename T>
 __global__ void __launch_bounds__(GJTH) k_gj_rowpanel(const T* A, T* B, int64_t n, int k, const T* Pinv,
@@ -148,13 +282,13 @@ __global__ void __launch_bounds__(GJTH) k_gj_rowpanel(const T* A, T* B, int64_t 
   const int tj = jj >= k ? jj + 1 : jj;
   const int64_t c0 = int64_t(tj) * GJB + h * GJH;
   if (tj >= nt || c0 >= n) return;
-  load_cols<GJTH>(Pinv, GJB, 0, 0, Ps, 1.f);
-  load_rows<GJH>(A, n, int64_t(k) * GJB, c0, Xs);
-  float acc[4][4];
-  zero_block(acc);
+  h_load_left(Pinv, GJB, 0, 0, Ps, 1.f);
+  h_load_right(A, n, int64_t(k) * GJB, c0, Xs);
+  float acc[8][4];
+  h_zero(acc);
   __syncthreads();
-  tile_fma<GJH>(Ps, Xs, acc);
-  store_block(acc, B, n, int64_t(k) * GJB, c0);
+  h_fma(Ps, Xs, acc);
+  h_store_block(acc, B, n, int64_t(k) * GJB, c0);
 }
 
 // Update of every half tile outside row k.  When skip_pivot is set, tile
@@ -171,18 +305,18 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
   if (skip_pivot && ti == k + 1 && tj == k + 1) return;
   const int64_t r0 = int64_t(ti) * GJB, c0 = int64_t(tj) * GJB + h * GJH;
   if (c0 >= n) return;
-  load_cols<GJTH>(A, n, r0, int64_t(k) * GJB, Ls, -1.f);   // -A[i,k]
-  float acc[4][4];
+  h_load_left(A, n, r0, int64_t(k) * GJB, Ls, -1.f);        // -A[i,k]
+  float acc[8][4];
   if (tj == k) {
-    load_rows<GJH>(Pinv, GJB, 0, h * GJH, Rs);
-    zero_block(acc);
+    h_load_right(Pinv, GJB, 0, h * GJH, Rs);
+    h_zero(acc);
   } else {
-    load_rows<GJH>(B, n, int64_t(k) * GJB, c0, Rs);         // B[k,j] from the row panel
-    load_block(A, n, r0, c0, acc);
+    h_load_right(B, n, int64_t(k) * GJB, c0, Rs);           // B[k,j] from the row panel
+    h_load_block(A, n, r0, c0, acc);
   }
   __syncthreads();
-  tile_fma<GJH>(Ls, Rs, acc);
-  store_block(acc, B, n, r0, c0);
+  h_fma(Ls, Rs, acc);
+  h_store_block(acc, B, n, r0, c0);
 }
 
 // The first kb0 tiles of the core lie inside its leading identity block
@@ -190,43 +324,45 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
 // (pivot I of size kb0 * GJB) maps A -> B as
 //     B[0:,0:] = I, B[0:, j] = A[0:, j], B[i, 0:] = -A[i, 0:],
 //     B[i, j] = A[i, j] - A[i, 0:] A[0:, j]      (tiles i, j >= kb0)
-// which replaces kb0 sweeps by one launch.  CTA = one output tile.
+// which replaces kb0 sweeps by one launch.  CTA = one output half tile.
 template <typename T>
-__global__ void __launch_bounds__(GJT) k_gj_identity(const T* A, T* B, int64_t n, int kb0, const int* skip) {
+__global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t n, int kb0, const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP];
+  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJH + 4];
   const int nt = int((n + GJB - 1) / GJB);
-  const int ti = blockIdx.x % nt, tj = blockIdx.x / nt;
-  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
-  const int64_t r0 = int64_t(ti) * GJB, c0 = int64_t(tj) * GJB;
-  float acc[4][4];
+  const int h = int(blockIdx.x) % 2, b = int(blockIdx.x) / 2;
+  const int ti = b % nt, tj = b / nt;
+  const int bi = threadIdx.x % 8, bj = threadIdx.x / 8;
+  const int64_t r0 = int64_t(ti) * GJB, c0 = int64_t(tj) * GJB + h * GJH;
+  if (c0 >= n) return;
+  float acc[8][4];
   if (ti < kb0 || tj < kb0) {
     if (ti < kb0 && tj < kb0) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = (r0 + 4 * bi + u == c0 + 4 * bj + v) ? 1.f : 0.f;
+        for (int v = 0; v < 4; ++v) acc[u][v] = (r0 + h_row(bi, u / 4) + u % 4 == c0 + 4 * bj + v) ? 1.f : 0.f;
     } else {
-      load_block(A, n, r0, c0, acc);
+      h_load_block(A, n, r0, c0, acc);
       if (ti >= kb0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u][v] = -acc[u][v];
       }
     }
-    store_block(acc, B, n, r0, c0);
+    h_store_block(acc, B, n, r0, c0);
     return;
   }
-  load_block(A, n, r0, c0, acc);
+  h_load_block(A, n, r0, c0, acc);
   for (int kk = 0; kk < kb0; ++kk) {
     __syncthreads();
-    load_cols<GJT>(A, n, r0, int64_t(kk) * GJB, Ls, -1.f);
-    load_rows<GJB>(A, n, int64_t(kk) * GJB, c0, Rs);
+    h_load_left(A, n, r0, int64_t(kk) * GJB, Ls, -1.f);
+    h_load_right(A, n, int64_t(kk) * GJB, c0, Rs);
     __syncthreads();
-    tile_fma<GJB>(Ls, Rs, acc);
+    h_fma(Ls, Rs, acc);
   }
-  store_block(acc, B, n, r0, c0);
+  h_store_block(acc, B, n, r0, c0);
 }
 
 // ---------------------------------------------------------------------------
@@ -389,7 +525,7 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
   int k0 = int(ident / GJB);
   if (k0 >= nt) k0 = nt - 1;
   if (k0 > 0) {
-    k_gj_identity<T><<<nt * nt, GJT, 0, s>>>(src, dst, n, k0, skip);
+    k_gj_identity<T><<<nt * nt * 2, GJTH, 0, s>>>(src, dst, n, k0, skip);
     T* t = src;
     src = dst;
     dst = t;

@@ -36,6 +36,40 @@ __device__ __forceinline__ bool warp_chol(double* G, double* rinv, int R) {
   return ok;
 }
 
+// The same factorisation by a whole CTA.  The pivot chain is latency-bound:
+// on this part a dependent float64 square root costs about 560 cycles and a
+// divide about 360, a reciprocal square root about 320.  So one thread takes
+// rsqrt of each pivot (L[k,k] = piv * rsqrt(piv), 1 / L[k,k] = rsqrt(piv),
+// each within a few ulp of the square root and its reciprocal) while the
+// others wait at a barrier, and the column scale and the trailing update are
+// spread over all threads.  ok_s is a shared-memory flag; the return value is
+// uniform over the CTA.
+__device__ __forceinline__ bool cta_chol(double* G, double* rinv, int R, int* ok_s) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) *ok_s = 1;
+  for (int k = 0; k < R; ++k) {
+    __syncthreads();
+    if (tid == 0) {
+      const double piv = G[k + R * k];
+      if (!(piv > 0.0) || !isfinite(piv)) *ok_s = 0;
+      const double ik = rsqrt(piv);
+      G[k + R * k] = piv * ik;
+      rinv[k] = ik;
+    }
+    __syncthreads();
+    const double ik = rinv[k];
+    const int m = R - k - 1;
+    for (int i = tid; i < m; i += nt) G[k + 1 + i + R * k] *= ik;
+    __syncthreads();
+    for (int q = tid; q < m * m; q += nt) {
+      const int i = k + 1 + q % m, l = k + 1 + q / m;
+      if (l <= i) G[i + R * l] = fma(-G[i + R * k], G[l + R * k], G[i + R * l]);
+    }
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
 // z <- L^{-1} z, one warp; rinv = 1 / diag(L).
 __device__ __forceinline__ void warp_fwd(const double* L, const double* rinv, double* z, int R) {
   const int lane = threadIdx.x & 31;

@@ -190,28 +190,61 @@ __global__ void __launch_bounds__(kUpdRows * 32) k_update(Dims d, const double* 
 
 __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_status* st,
                           double* scal, int* info, double* scale) {
-  __shared__ double sh[256];
-  __shared__ double norms[CP_MAX_N * CP_MAX_R];
-  __shared__ int s_acc;
+  // One CTA of 256 threads.  The float64 square roots, divides and roots
+  // below are long dependent operations on this part (hundreds of cycles
+  // each), so independent ones run on different threads: the two relative
+  // errors and the refinement residual on three threads, the column norms
+  // on one thread per (mode, column), the accept / damping decision on a
+  // thread of the last warp, while the equal-energy targets are formed for
+  // every column and applied only if the step is accepted.
+  constexpr int kT = 256;
+  __shared__ double sh[kT];
+  __shared__ double qs[kT];
+  __shared__ double nrm[CP_MAX_N * CP_MAX_R], rnm[CP_MAX_N * CP_MAX_R], tgt[CP_MAX_R];
+  __shared__ double e_s[2], rr_s;
+  __shared__ int sweeps_s, s_acc;
   if (st->stop != CP_RUNNING) return;
   const int tid = threadIdx.x;
-  const int R = d.R, N = d.N;
+  const int R = d.R, N = d.N, NR = d.N * d.R;
   double v = 0.0;
-  for (int64_t c = tid; c < nparts; c += 256) v += part[c * (1 + R)];
-  const double den = block_sum<256>(v, sh);
-  // column norms of the trial factors, per mode, summed in CTA order
-  if (tid < N * R) {
-    const int n = tid / R, r = tid % R;
+  for (int64_t c = tid; c < nparts; c += kT) v += part[c * (1 + R)];
+  const double den = block_sum<kT>(v, sh);
+  // squared column norms of the trial factors, tp threads per (mode, column),
+  // each summing every tp-th block of its mode
+  int tp = 1;
+  while (tp * 2 * NR <= kT) tp *= 2;
+  if (tid < NR * tp) {
+    const int pr = tid / tp, sub = tid % tp, n = pr / R, r = pr % R;
     int64_t c0 = 0;
     for (int k = 0; k < n; ++k) c0 += (d.I[k] + kUpdRows - 1) / kUpdRows;
     const int64_t c1 = c0 + (d.I[n] + kUpdRows - 1) / kUpdRows;
-    double s = 0.0;
-#pragma unroll 8
-    for (int64_t c = c0; c < c1; ++c) s += part[c * (1 + R) + 1 + r];
-    norms[tid] = s;
+    double sq = 0.0;
+    for (int64_t c = c0 + sub; c < c1; c += tp) sq += part[c * (1 + R) + 1 + r];
+    qs[tid] = sq;
+  }
+  const int tdec = kT - 1;   // decision thread, last warp
+  if (tid == kT - 32) e_s[0] = sqrt(st->resid2 / st->y_norm2);
+  if (tid == kT - 64) e_s[1] = sqrt(scal[SC_R2T] / st->y_norm2);
+  if (tid == kT - 96) {
+    double rr = 0.0;   // relative residual of the last refinement sweep that ran
+    int sweeps = 0;
+    for (int k = kMaxRefine; k >= 1; --k)
+      if (scal[SC_NRM + k] > 0.0) {
+        rr = sqrt(scal[SC_NRM + k] / scal[SC_NRM]);
+        sweeps = k;
+        break;
+      }
+    rr_s = rr;
+    sweeps_s = sweeps;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid < NR) {
+    double sq = 0.0;
+    for (int q = 0; q < tp; ++q) sq += qs[tid * tp + q];
+    nrm[tid] = sqrt(sq);
+    rnm[tid] = rsqrt(sq);
+  }
+  if (tid == tdec) {
     const double r2 = st->resid2;
     const double r2t = scal[SC_R2T];
     const int bad = info[IN_INFO];
@@ -232,27 +265,17 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
     st->denom = den;
     st->resid2_trial = r2t;
     st->info = bad;
-    {
-      double rr = 0.0;   // relative residual of the last refinement sweep that ran
-      int sweeps = 0;
-      for (int k = kMaxRefine; k >= 1; --k)
-        if (scal[SC_NRM + k] > 0.0) {
-          rr = sqrt(scal[SC_NRM + k] / scal[SC_NRM]);
-          sweeps = k;
-          break;
-        }
-      st->refine_resid = rr;
-      st->refine_sweeps = sweeps;
-    }
+    st->refine_resid = rr_s;
+    st->refine_sweeps = sweeps_s;
     st->mu = mu;
     st->nu = nu;
     st->last_accepted = accept ? 1 : 0;
     if (accept) {
-      const double e_old = sqrt(r2 / st->y_norm2), e_new = sqrt(r2t / st->y_norm2);
+      const double e_old = e_s[0], e_new = e_s[1];
       st->accepted += 1;
       st->resid2 = r2t;
       st->rel_err = e_new;
-      if (e_old > 0.0 && fabs(e_old - e_new) / e_old < o.tol) st->stop = CP_STOP_TOL;
+      if (e_old > 0.0 && fabs(e_old - e_new) < o.tol * e_old) st->stop = CP_STOP_TOL;
     }
     if (st->stop == CP_RUNNING && mu > o.mu_max) st->stop = CP_STOP_MU;
     if (st->stop == CP_RUNNING && st->iters >= o.max_iter) st->stop = CP_STOP_MAXIT;
@@ -262,16 +285,20 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
   __syncthreads();
   // equal-energy scales: s_r^(n) = lambda_r^(1/N) / ||a_r^(n)||, lambda_r = prod_n ||a_r^(n)||
   if (tid < R) {
-    const int r = tid;
-    bool ok = (o.normalize != 0) && s_acc;
     double lam = 1.0;
+    bool pos = true;
     for (int n = 0; n < N; ++n) {
-      const double nr = sqrt(norms[n * R + r]);
-      if (!(nr > 0.0)) ok = false;
+      const double nr = nrm[n * R + tid];
+      if (!(nr > 0.0)) pos = false;
       lam *= nr;
     }
-    const double tgt = ok ? pow(lam, 1.0 / N) : 1.0;
-    for (int n = 0; n < N; ++n) scale[n * R + r] = ok ? tgt / sqrt(norms[n * R + r]) : 1.0;
+    tgt[tid] = !pos ? 0.0 : (N == 2 ? sqrt(lam) : (N == 3 ? cbrt(lam) : pow(lam, 1.0 / N)));
+  }
+  __syncthreads();
+  if (tid < NR) {
+    const int r = tid % R;
+    const bool ok = (o.normalize != 0) && s_acc && tgt[r] > 0.0;
+    scale[tid] = ok ? tgt[r] * rnm[tid] : 1.0;
   }
 }
 
