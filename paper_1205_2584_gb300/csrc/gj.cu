@@ -271,33 +271,124 @@ __device__ __forceinline__ void h_fma(const float (*Ls)[GJP], const float (*Rs)[
   }
 }
 
+// ---- asynchronous operand copies (n % 4 == 0) ----
+
+// 16-byte global -> shared copy that bypasses registers; when !pred the
+// destination is zero-filled and nothing is read.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Ls[l][r] = A(r0 + r, c0 + l) and Rc[c][l] = A(k0 + l, c1 + c) (both copied
+// column by column, rows contiguous), r, l < 64, c < 32; 64 threads.
+__device__ __forceinline__ void h_copy_operands(const float* A, int64_t n, int64_t r0, int64_t c0, int64_t k0,
+                                                int64_t c1, float (*Ls)[GJP], float (*Rc)[GJP]) {
+#pragma unroll 4
+  for (int q = 0; q < GJB * GJB / 4 / GJTH; ++q) {
+    const int e = int(threadIdx.x) + q * GJTH;
+    const int r = 4 * (e % 16), l = e / 16;
+    const int64_t gr = r0 + r, gc = c0 + l;
+    const bool in = gr < n && gc < n;
+    cp_async16(&Ls[l][r], in ? A + gr + n * gc : A, in);
+  }
+#pragma unroll 4
+  for (int q = 0; q < GJB * GJH / 4 / GJTH; ++q) {
+    const int e = int(threadIdx.x) + q * GJTH;
+    const int l = 4 * (e % 16), c = e / 16;
+    const int64_t gr = k0 + l, gc = c1 + c;
+    const bool in = gr < n && gc < n;
+    cp_async16(&Rc[c][l], in ? A + gr + n * gc : A, in);
+  }
+}
+
+// x += SGN L R with L = Ls (64 x 64, k-major) and R stored by columns in Rc
+// (Rc[c][l] = R[l][c]); four k-steps per float4 of R.
+template <int SGN>
+__device__ __forceinline__ void h_fma_rc(const float (*Ls)[GJP], const float (*Rc)[GJP], float (&x)[8][4]) {
+  const int bi = threadIdx.x % 8, bj = threadIdx.x / 8;
+#pragma unroll 2
+  for (int l4 = 0; l4 < GJB; l4 += 4) {
+    float rv[4][4];                  // rv[v][dl] = R[l4 + dl][4 bj + v]
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float4 t = *reinterpret_cast<const float4*>(&Rc[4 * bj + v][l4]);
+      rv[v][0] = t.x;
+      rv[v][1] = t.y;
+      rv[v][2] = t.z;
+      rv[v][3] = t.w;
+    }
+#pragma unroll
+    for (int dl = 0; dl < 4; ++dl) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&Ls[l4 + dl][4 * bi]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Ls[l4 + dl][32 + 4 * bi]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[u][v] = fmaf(SGN > 0 ? av[u] : -av[u], rv[v][dl], x[u][v]);
+    }
+  }
+}
+
 // Row panel: B[k,j] = P^{-1} A[k,j] for j != k; CTA = one half tile of row k.
-template <typename T>
+// ASYNC (n % 4 == 0): operands copied with cp.async, R kept by columns.
+constexpr int kTileSmem = 2 * GJB * GJP * 4;   // (Ls, Rc) or (Ls, Rs)
+template <typename T, bool ASYNC>
 __global__ void __launch_bounds__(GJTH) k_gj_rowpanel(const T* A, T* B, int64_t n, int k, const T* Pinv,
                                                       const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ps[GJB][GJP], Xs[GJB][GJH + 4];
+  extern __shared__ __align__(16) float dsm[];
+  float (*Ps)[GJP] = reinterpret_cast<float (*)[GJP]>(dsm);
   const int nt = int((n + GJB - 1) / GJB);
   const int jj = int(blockIdx.x) / 2, h = int(blockIdx.x) % 2;
   const int tj = jj >= k ? jj + 1 : jj;
   const int64_t c0 = int64_t(tj) * GJB + h * GJH;
   if (tj >= nt || c0 >= n) return;
-  h_load_left(Pinv, GJB, 0, 0, Ps, 1.f);
-  h_load_right(A, n, int64_t(k) * GJB, c0, Xs);
   float acc[8][4];
   h_zero(acc);
-  __syncthreads();
-  h_fma(Ps, Xs, acc);
+  if (ASYNC) {
+    float (*Rc)[GJP] = Ps + GJB;
+#pragma unroll 4
+    for (int q = 0; q < GJB * GJB / 4 / GJTH; ++q) {          // Ps[l][r] = P^{-1}(r, l)
+      const int e = int(threadIdx.x) + q * GJTH;
+      const int r = 4 * (e % 16), l = e / 16;
+      cp_async16(&Ps[l][r], Pinv + r + GJB * l, true);
+    }
+#pragma unroll 4
+    for (int q = 0; q < GJB * GJH / 4 / GJTH; ++q) {          // Rc[c][l] = A(64 k + l, c0 + c)
+      const int e = int(threadIdx.x) + q * GJTH;
+      const int l = 4 * (e % 16), c = e / 16;
+      const int64_t gr = int64_t(k) * GJB + l, gc = c0 + c;
+      const bool in = gr < n && gc < n;
+      cp_async16(&Rc[c][l], in ? A + gr + n * gc : A, in);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    h_fma_rc<1>(Ps, Rc, acc);
+  } else {
+    float (*Xs)[GJH + 4] = reinterpret_cast<float (*)[GJH + 4]>(dsm + GJB * GJP);
+    h_load_left(Pinv, GJB, 0, 0, Ps, 1.f);
+    h_load_right(A, n, int64_t(k) * GJB, c0, Xs);
+    __syncthreads();
+    h_fma(Ps, Xs, acc);
+  }
   h_store_block(acc, B, n, int64_t(k) * GJB, c0);
 }
 
 // Update of every half tile outside row k.  When skip_pivot is set, tile
 // (k+1, k+1) is left to k_gj_pivot_next (which runs concurrently).
-template <typename T>
+template <typename T, bool ASYNC>
 __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n, int k, const T* Pinv,
                                                     int skip_pivot, const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJH + 4];
+  extern __shared__ __align__(16) float dsm[];
+  float (*Ls)[GJP] = reinterpret_cast<float (*)[GJP]>(dsm);
   const int nt = int((n + GJB - 1) / GJB);
   const int h = int(blockIdx.x) % 2, b = int(blockIdx.x) / 2;
   const int ti = b % (nt - 1) >= k ? b % (nt - 1) + 1 : b % (nt - 1);
@@ -305,17 +396,49 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
   if (skip_pivot && ti == k + 1 && tj == k + 1) return;
   const int64_t r0 = int64_t(ti) * GJB, c0 = int64_t(tj) * GJB + h * GJH;
   if (c0 >= n) return;
-  h_load_left(A, n, r0, int64_t(k) * GJB, Ls, -1.f);        // -A[i,k]
+  const int64_t ko = int64_t(k) * GJB;
   float acc[8][4];
-  if (tj == k) {
-    h_load_right(Pinv, GJB, 0, h * GJH, Rs);
-    h_zero(acc);
+  if (ASYNC) {
+    float (*Rc)[GJP] = Ls + GJB;
+#pragma unroll 4
+    for (int q = 0; q < GJB * GJB / 4 / GJTH; ++q) {          // Ls[l][r] = A(r0 + r, 64 k + l)
+      const int e = int(threadIdx.x) + q * GJTH;
+      const int r = 4 * (e % 16), l = e / 16;
+      const int64_t gr = r0 + r, gc = ko + l;
+      const bool in = gr < n && gc < n;
+      cp_async16(&Ls[l][r], in ? A + gr + n * gc : A, in);
+    }
+#pragma unroll 4
+    for (int q = 0; q < GJB * GJH / 4 / GJTH; ++q) {          // Rc[c][l] = B(64 k + l, c0 + c) or P^{-1}
+      const int e = int(threadIdx.x) + q * GJTH;
+      const int l = 4 * (e % 16), c = e / 16;
+      if (tj == k) {
+        cp_async16(&Rc[c][l], Pinv + l + GJB * (h * GJH + c), true);
+      } else {
+        const int64_t gr = ko + l, gc = c0 + c;
+        const bool in = gr < n && gc < n;
+        cp_async16(&Rc[c][l], in ? B + gr + n * gc : B, in);
+      }
+    }
+    cp_async_commit();
+    if (tj == k) h_zero(acc);
+    else h_load_block(A, n, r0, c0, acc);
+    cp_async_wait<0>();
+    __syncthreads();
+    h_fma_rc<-1>(Ls, Rc, acc);                               // - A[i,k] B[k,j]
   } else {
-    h_load_right(B, n, int64_t(k) * GJB, c0, Rs);           // B[k,j] from the row panel
-    h_load_block(A, n, r0, c0, acc);
+    float (*Rs)[GJH + 4] = reinterpret_cast<float (*)[GJH + 4]>(dsm + GJB * GJP);
+    h_load_left(A, n, r0, ko, Ls, -1.f);                      // -A[i,k]
+    if (tj == k) {
+      h_load_right(Pinv, GJB, 0, h * GJH, Rs);
+      h_zero(acc);
+    } else {
+      h_load_right(B, n, ko, c0, Rs);                         // B[k,j] from the row panel
+      h_load_block(A, n, r0, c0, acc);
+    }
+    __syncthreads();
+    h_fma(Ls, Rs, acc);
   }
-  __syncthreads();
-  h_fma(Ls, Rs, acc);
   h_store_block(acc, B, n, r0, c0);
 }
 
@@ -325,10 +448,14 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
 //     B[0:,0:] = I, B[0:, j] = A[0:, j], B[i, 0:] = -A[i, 0:],
 //     B[i, j] = A[i, j] - A[i, 0:] A[0:, j]      (tiles i, j >= kb0)
 // which replaces kb0 sweeps by one launch.  CTA = one output half tile.
-template <typename T>
+// ASYNC (n % 4 == 0): the K loop of an interior tile copies the operands of
+// step kk + 1 (cp.async, two shared-memory stages in dynamic shared memory)
+// while it multiplies those of step kk.
+constexpr int kIdentSmem = 2 * 2 * GJB * GJP * 4;   // two stages of (Ls, Rc)
+template <typename T, bool ASYNC>
 __global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t n, int kb0, const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJH + 4];
+  extern __shared__ __align__(16) float dsm[];
   const int nt = int((n + GJB - 1) / GJB);
   const int h = int(blockIdx.x) % 2, b = int(blockIdx.x) / 2;
   const int ti = b % nt, tj = b / nt;
@@ -354,13 +481,39 @@ __global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t 
     h_store_block(acc, B, n, r0, c0);
     return;
   }
-  h_load_block(A, n, r0, c0, acc);
-  for (int kk = 0; kk < kb0; ++kk) {
-    __syncthreads();
-    h_load_left(A, n, r0, int64_t(kk) * GJB, Ls, -1.f);
-    h_load_right(A, n, int64_t(kk) * GJB, c0, Rs);
-    __syncthreads();
-    h_fma(Ls, Rs, acc);
+  if (ASYNC) {
+    float (*Ls0)[GJP] = reinterpret_cast<float (*)[GJP]>(dsm);
+    float (*Rc0)[GJP] = Ls0 + GJB;
+    float (*Ls1)[GJP] = Rc0 + GJB;
+    float (*Rc1)[GJP] = Ls1 + GJB;
+    h_copy_operands(A, n, r0, 0, 0, c0, Ls0, Rc0);
+    cp_async_commit();
+    h_load_block(A, n, r0, c0, acc);
+    for (int kk = 0; kk < kb0; ++kk) {
+      const bool odd = kk & 1;
+      if (kk + 1 < kb0) {
+        h_copy_operands(A, n, r0, int64_t(kk + 1) * GJB, int64_t(kk + 1) * GJB, c0, odd ? Ls0 : Ls1,
+                        odd ? Rc0 : Rc1);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      h_fma_rc<-1>(odd ? Ls1 : Ls0, odd ? Rc1 : Rc0, acc);
+      __syncthreads();
+    }
+  } else {
+    float (*Ls)[GJP] = reinterpret_cast<float (*)[GJP]>(dsm);
+    float (*Rs)[GJH + 4] = reinterpret_cast<float (*)[GJH + 4]>(dsm + GJB * GJP);
+    h_load_block(A, n, r0, c0, acc);
+    for (int kk = 0; kk < kb0; ++kk) {
+      __syncthreads();
+      h_load_left(A, n, r0, int64_t(kk) * GJB, Ls, -1.f);
+      h_load_right(A, n, int64_t(kk) * GJB, c0, Rs);
+      __syncthreads();
+      h_fma(Ls, Rs, acc);
+    }
   }
   h_store_block(acc, B, n, r0, c0);
 }
@@ -525,7 +678,15 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
   int k0 = int(ident / GJB);
   if (k0 >= nt) k0 = nt - 1;
   if (k0 > 0) {
-    k_gj_identity<T><<<nt * nt * 2, GJTH, 0, s>>>(src, dst, n, k0, skip);
+    if (n % 4 == 0) {
+      if (cudaFuncSetAttribute(k_gj_identity<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kIdentSmem) != cudaSuccess)
+        return CP_ECUDA;
+      k_gj_identity<T, true><<<nt * nt * 2, GJTH, kIdentSmem, s>>>(src, dst, n, k0, skip);
+    } else {
+      k_gj_identity<T, false><<<nt * nt * 2, GJTH, (GJB * GJP + GJB * (GJH + 4)) * 4, s>>>(src, dst, n, k0,
+                                                                                           skip);
+    }
     T* t = src;
     src = dst;
     dst = t;
@@ -542,8 +703,15 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
         k_gj_pivot_next<T><<<1, GJT, kPivotReserve, side>>>(src, n, k, pk, pn, info, skip);
         if (cudaEventRecord(ev_join, side) != cudaSuccess) return CP_ECUDA;
       }
-      k_gj_rowpanel<T><<<(nt - 1) * 2, GJTH, 0, s>>>(src, dst, n, k, pk, skip);
-      k_gj_update<T><<<(nt - 1) * nt * 2, GJTH, 0, s>>>(src, dst, n, k, pk, (next && side) ? 1 : 0, skip);
+      if (n % 4 == 0) {
+        k_gj_rowpanel<T, true><<<(nt - 1) * 2, GJTH, kTileSmem, s>>>(src, dst, n, k, pk, skip);
+        k_gj_update<T, true><<<(nt - 1) * nt * 2, GJTH, kTileSmem, s>>>(src, dst, n, k, pk,
+                                                                        (next && side) ? 1 : 0, skip);
+      } else {
+        k_gj_rowpanel<T, false><<<(nt - 1) * 2, GJTH, kTileSmem, s>>>(src, dst, n, k, pk, skip);
+        k_gj_update<T, false><<<(nt - 1) * nt * 2, GJTH, kTileSmem, s>>>(src, dst, n, k, pk,
+                                                                         (next && side) ? 1 : 0, skip);
+      }
       if (next && side) {
         if (cudaStreamWaitEvent(s, ev_join, 0) != cudaSuccess) return CP_ECUDA;
       } else if (next) {
