@@ -90,15 +90,36 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& x0, __nv_bfloat16
   x2 = __float2bfloat16_rn(r1 - __bfloat162float(x1));
 }
 
-__device__ __forceinline__ void split3d(double x, __nv_bfloat16& x0, __nv_bfloat16& x1, __nv_bfloat16& x2) {
-  x0 = __double2bfloat16(x);
-  const double r1 = x - double(__bfloat162float(x0));
-  x1 = __double2bfloat16(r1);
-  x2 = __double2bfloat16(r1 - double(__bfloat162float(x1)));
-}
-
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return uint32_t(__bfloat16_as_ushort(lo)) | (uint32_t(__bfloat16_as_ushort(hi)) << 16);
+}
+
+// Pieces of row `row` of the A1 chunk (i1 = row index in A1): the R factor
+// values are all loaded first, rounded once to float32 and split into three
+// bfloat16 pieces in float32 arithmetic.  A float64 split would run its
+// conversions and subtractions on this part's float64 pipe (about 2 results
+// per clock per SM), which made the per-CTA setup of the pass cost ~10 us.
+__device__ __forceinline__ void build_a1_row(const double* a, int64_t I1, int R, int i1, int row,
+                                             unsigned char* apc) {
+  float v[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) v[r] = (i1 < I1 && r < R) ? float(a[i1 + I1 * r]) : 0.f;
+#pragma unroll
+  for (int rg = 0; rg < 4; ++rg) {
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      __nv_bfloat16 x0[2], x1[2], x2[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) split3(v[rg * 8 + h * 2 + q], x0[q], x1[q], x2[q]);
+      w0[h] = pack2(x0[0], x0[1]);
+      w1[h] = pack2(x1[0], x1[1]);
+      w2[h] = pack2(x2[0], x2[1]);
+    }
+    *reinterpret_cast<uint4*>(apc + coff(row, rg * 8, kArow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    *reinterpret_cast<uint4*>(apc + coff(row, 32 + rg * 8, kArow)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4*>(apc + coff(row, 64 + rg * 8, kArow)) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  }
 }
 
 // lane l returns the sum over the warp of v[l] (recursive halving, 31 shuffles)
@@ -209,27 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
     uint4* z = reinterpret_cast<uint4*>(ypc);
     for (int e = tid; e < 2 * kYpcBytes / 16; e += 128) z[e] = make_uint4(0, 0, 0, 0);
     // A1 chunk pieces, row t = i1 - i1_0, piece-interleaved (see kArow)
-    const int i1 = i1_0 + tid;
-#pragma unroll 1
-    for (int rg = 0; rg < 4; ++rg) {
-      uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        __nv_bfloat16 x0[2], x1[2], x2[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int r = rg * 8 + h * 2 + q;
-          const double v = (i1 < p.I1 && r < R) ? p.a[i1 + int64_t(p.I1) * r] : 0.0;
-          split3d(v, x0[q], x1[q], x2[q]);
-        }
-        w0[h] = pack2(x0[0], x0[1]);
-        w1[h] = pack2(x1[0], x1[1]);
-        w2[h] = pack2(x2[0], x2[1]);
-      }
-      *reinterpret_cast<uint4*>(apc + coff(tid, rg * 8, kArow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-      *reinterpret_cast<uint4*>(apc + coff(tid, 32 + rg * 8, kArow)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-      *reinterpret_cast<uint4*>(apc + coff(tid, 64 + rg * 8, kArow)) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-    }
+    build_a1_row(p.a, p.I1, R, i1_0 + tid, tid, apc);
     const int i2 = i2_0 + tid;
     const double* A2 = p.a + int64_t(p.I1) * R;
 #pragma unroll
@@ -593,27 +594,7 @@ __global__ void __launch_bounds__(kTcThreads3, 1)
   }
   if (warp < 4) {
     // A1 chunk pieces (rows i1 - i1_0), piece-interleaved
-    const int i1 = i1_0 + row;
-#pragma unroll 1
-    for (int rg = 0; rg < 4; ++rg) {
-      uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        __nv_bfloat16 x0[2], x1[2], x2[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int r = rg * 8 + h * 2 + q;
-          const double v = (i1 < p.I1 && r < R) ? p.a[i1 + int64_t(p.I1) * r] : 0.0;
-          split3d(v, x0[q], x1[q], x2[q]);
-        }
-        w0[h] = pack2(x0[0], x0[1]);
-        w1[h] = pack2(x1[0], x1[1]);
-        w2[h] = pack2(x2[0], x2[1]);
-      }
-      *reinterpret_cast<uint4*>(apc + coff(row, rg * 8, kArow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-      *reinterpret_cast<uint4*>(apc + coff(row, 32 + rg * 8, kArow)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-      *reinterpret_cast<uint4*>(apc + coff(row, 64 + rg * 8, kArow)) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-    }
+    build_a1_row(p.a, p.I1, R, i1_0 + row, row, apc);
   }
   if (warp == 6) {
     a3s[0][lane] = (lane < R) ? float(A3[s0 + int64_t(p.I3) * lane]) : 0.f;
