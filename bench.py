@@ -49,6 +49,10 @@ L2_FLUSH_BYTES = 256 << 20
 # the ncu captures summarised in profiles/k_mttkrp_tc3_bf16x2.md (bytes)
 TRAFFIC_200 = 32.293376e6
 TRAFFIC_512 = 537.939712e6 + 3.137536e6
+# dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one core
+# inverse (n = 1200), from the ncu capture summarised in
+# profiles/k_gj_inverse_traffic.md (bytes; every kernel with cold caches under ncu)
+GJ_TRAFFIC = 88.605952e6
 # timed runs restart from their initial factors every this many launches
 RESTART_EVERY = 50
 
@@ -239,6 +243,77 @@ def oracle_rate(problem, seconds: float):
     return res.iters / dt, res.iters, dt
 
 
+# FP32 multiply-add lanes per SM and SM count of a GB300 (derived ALU peak:
+# SMs x lanes x 2 flops x maximum SM clock)
+FP32_FMA_PER_SM_CLK = 128
+GB300_SMS = 152
+
+
+def gj_inverse_flops(n: int, ident: int, b: int = 64) -> int:
+    """Algorithmic flops of the blocked Gauss-Jordan inverse of an n x n
+    matrix whose leading ident rows are the identity (eliminated at once):
+    the identity step updates the (n - e)^2 trailing block with depth e;
+    every later sweep with panel width w does the rank-w update of the n - w
+    rows outside the panel (all n columns), the row panel P^{-1} A[k, :]
+    and forms (two w^3 products) and inverts (w^3) its pivot block."""
+    nt = (n + b - 1) // b
+    k0 = min(ident // b, nt - 1)
+    e = k0 * b
+    fma = (n - e) ** 2 * e
+    for k in range(k0, nt):
+        w = min(b, n - k * b)
+        fma += (n - w) * n * w + w * w * (n - w) + 3 * w ** 3
+    return 2 * fma
+
+
+def core_inverse_roofline(cp, torch, flush, peaks, peak_src, seed, reps=20):
+    """cp_spd_invert_f32 timed live on an SPD matrix shaped like the
+    benchmark's core (n = N R^2 = 1200, identity diagonal R^2 x R^2 blocks),
+    L2 flushed and the input restored between launches (outside the events).
+    The call is captured once in a CUDA graph and the replays are timed, as
+    inside the step's graph (host launch overhead is not device time)."""
+    import numpy as np
+    n, blk = len(DIMS) * R * R, R * R
+    rng = np.random.default_rng(seed + 17)
+    X = rng.standard_normal((n, n))
+    X = X + X.T
+    for b0 in range(0, n, blk):
+        X[b0:b0 + blk, b0:b0 + blk] = 0.0
+    X *= 0.45 / np.linalg.norm(X, 2)
+    M = torch.from_numpy((np.eye(n) + X).astype(np.float32).ravel(order="F").copy()).cuda()
+    A = torch.empty_like(M)
+    inv = cp.SpdInverse(n, blk)
+    for _ in range(3):
+        A.copy_(M)
+        inv.run(A)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    A.copy_(M)
+    with torch.cuda.graph(g, stream=torch.cuda.current_stream()):
+        inv.run(A)
+    evs = []
+    for _ in range(reps):
+        A.copy_(M)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    flops = gj_inverse_flops(n, blk)
+    peak = GB300_SMS * FP32_FMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "k_gj_* (float32 Gauss-Jordan inverse of the core, one call)",
+            "workload": f"n = N R^2 = {n}, identity {blk} x {blk} blocks, SPD", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": GJ_TRAFFIC,
+            "ms_per_launch": ms, "algorithmic_flops": flops,
+            "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x max SM clock",
+            "note": "latency-bound pivot chain (13 sweeps of 64 dependent elimination steps); "
+                    "the tensor pass is reported in roofline_tensor_pass"}
+
+
 def oracle_rate_one_thread(seed: int, seconds: float):
     """oracle_rate on one host thread: a child interpreter with the BLAS and
     OpenMP pools limited to one thread before numpy loads."""
@@ -390,7 +465,7 @@ def _run_ours(args, rank, world, local):
         mt_ms = time_pass(shape2, Y2, a_in)
         bytes_alg = int(np.prod(DIMS)) * 4
         achieved = bytes_alg / (mt_ms * 1e-3) / 1e9
-        out["roofline"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3 (all-mode MTTKRP + direct residual, one pass)",
+        out["roofline_tensor_pass"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3 (all-mode MTTKRP + direct residual, one pass)",
                            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                            "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_200,
                            "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": mt_ms,
@@ -406,6 +481,8 @@ def _run_ours(args, rank, world, local):
                                  "achieved": bbig / (big_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": bbig / (big_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                  "ms_per_launch": big_ms, "algorithmic_bytes": bbig, "traffic": TRAFFIC_512}
+        # --- the dominant kernel sequence of the step: the float32 core inverse ---
+        out["roofline"] = core_inverse_roofline(cp, torch, flush, peaks, peak_src, seed)
         del Ybig, abig
         # the float32-tensor form of the same step (tensor-core pass with an
         # exact float32 residual)

@@ -211,6 +211,28 @@ int cp_dgn_solve(const cp_shape* shape, const double* a, const double* mu, doubl
                  const double* w, double* f, int* info, void* ws, size_t ws_bytes,
                  void* stream);
 
+/* Float32 inverse of an n x n symmetric positive definite matrix by blocked
+ * Gauss-Jordan elimination: the core-system inverse of the mixed solve
+ * (CP_CORE_MIXED; the float64 refinement of cp_dgn_step then recovers the
+ * float64 solution of Theorem 1, Eq. inverse_f1a, with it).  No pivoting
+ * (each pivot block is a Schur complement of an SPD matrix).
+ *   A      (in, destroyed): n x n float32, column-major, full storage;
+ *          16-byte aligned; when ident > 0 its leading ident x ident block
+ *          must be the identity (it is eliminated in one step; the core's
+ *          diagonal R^2 x R^2 blocks are the identity).
+ *   work   n x n float32, 16-byte aligned, not overlapping A.
+ *   pinv   2 x 64 x 64 float32 of scratch.
+ *   info   device int (may be NULL): receives 0, or the 1-based index of
+ *          the first non-positive or non-finite pivot (the result is then
+ *          not an inverse).
+ *   in_work  host int: receives 1 if the inverse is left in work, 0 if in A
+ *          (fixed by n and ident, known before the device work runs).
+ * Enqueued on `stream`; the pivot chain runs on a second stream of the
+ * library, forked from and joined back to `stream` (graph-capturable).
+ * CP_EINVAL for null pointers, n < 1, ident < 0 or ident > n. */
+int cp_spd_invert_f32(int64_t n, int64_t ident, float* A, float* work, float* pinv, int* info,
+                      int* in_work, void* stream);
+
 /* ---- one Levenberg-Marquardt trial on the device (Algorithm 1, Sec. 4.6) ---- */
 
 /* Create a host handle for one decomposition.  a: the caller's float64

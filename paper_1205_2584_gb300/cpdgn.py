@@ -84,6 +84,8 @@ _sig = {
     "cp_batch_run": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                      ctypes.c_int, _vp, _vp],
     "cp_tensor_split": [_vp, ctypes.c_int64, _vp, _vp],
+    "cp_spd_invert_f32": [ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int),
+                          _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -179,6 +181,27 @@ def tensor_split(y32: torch.Tensor, out: Optional[torch.Tensor] = None, stream=N
         out = torch.empty(2 * J, dtype=torch.bfloat16, device=y32.device)
     _check(_lib.cp_tensor_split(_ptr(y32), J, _ptr(out), _stream(stream)), "cp_tensor_split")
     return out
+
+
+class SpdInverse:
+    """Buffers of cp_spd_invert_f32 for n x n matrices: `run(A)` inverts the
+    float32 column-major SPD matrix A in place of its buffer (A is destroyed)
+    and returns the device tensor holding the inverse (A's storage or the
+    work buffer) and the device pivot flag."""
+
+    def __init__(self, n: int, ident: int = 0, device="cuda"):
+        self.n, self.ident = int(n), int(ident)
+        self.work = torch.empty(self.n * self.n, dtype=torch.float32, device=device)
+        self.pinv = torch.empty(2 * 64 * 64, dtype=torch.float32, device=device)
+        self.info = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def run(self, A: torch.Tensor, stream=None):
+        assert A.dtype == torch.float32 and A.is_cuda and A.is_contiguous() and A.numel() == self.n * self.n
+        in_work = ctypes.c_int(0)
+        _check(_lib.cp_spd_invert_f32(self.n, self.ident, _ptr(A), _ptr(self.work), _ptr(self.pinv),
+                                      _ptr(self.info), ctypes.byref(in_work), _stream(stream)),
+               "cp_spd_invert_f32")
+        return (self.work if in_work.value else A), self.info
 
 
 # ---------------------------------------------------------------------------

@@ -29,6 +29,8 @@
 // so each k-step reads two float4 of the left operand and one of the right
 // operand for 32 multiply-adds; eight consecutive lanes read eight
 // consecutive float4, free of shared-memory bank conflicts.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cpdgn {
@@ -777,3 +779,32 @@ int launch_gemv_acc(const float* X, int64_t n, const double* r, double* y, const
 }
 
 }  // namespace cpdgn
+
+// One side stream and a fork/join event pair for every cp_spd_invert_f32
+// call of the process, created on first use; calls are serialised by the
+// mutex while they enqueue (the device work of consecutive calls on
+// different streams is ordered by the events).
+static std::mutex g_inv_mu;
+static cudaStream_t g_inv_side = nullptr;
+static cudaEvent_t g_inv_fork = nullptr, g_inv_join = nullptr;
+
+extern "C" int cp_spd_invert_f32(int64_t n, int64_t ident, float* A, float* work, float* pinv, int* info,
+                                 int* in_work, void* stream) {
+  if (!A || !work || !pinv || !in_work || n < 1 || ident < 0 || ident > n) return CP_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(work) & 15)) return CP_EINVAL;
+  std::lock_guard<std::mutex> lock(g_inv_mu);
+  if (!g_inv_side) {
+    if (cudaStreamCreateWithFlags(&g_inv_side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g_inv_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g_inv_join, cudaEventDisableTiming) != cudaSuccess)
+      return CP_ECUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (info && cudaMemsetAsync(info, 0, sizeof(int), s) != cudaSuccess) return CP_ECUDA;
+  float* res = nullptr;
+  const int rc = cpdgn::gj_invert<float>(A, work, pinv, n, ident, info, nullptr, s, g_inv_side, g_inv_fork,
+                                         g_inv_join, &res);
+  if (rc != CP_OK) return rc;
+  *in_work = (res == work) ? 1 : 0;
+  return CP_OK;
+}
