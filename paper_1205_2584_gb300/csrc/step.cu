@@ -376,12 +376,17 @@ __global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double
 // to refine_iters sweeps y += X (b - y - S^T K S y) with the float64
 // operator, stopping once ||b - core y|| <= 1e-15 ||b|| or the residual stops
 // shrinking (kernels of later sweeps return at once; the graph is fixed).
+// b = S^T (K w), ||b||^2 (nrm[0]) and K w, the right-hand side of the core
+// system; it needs the per-mode preparation only, not the core.
+static int core_rhs(const Dims& d, const Bufs& B, const int* skip, cudaStream_t s) {
+  return launch_apply_ST(d, B.LC, B.U, B.Gnm, B.w, 1, nullptr, nullptr, B.b, B.Kw, B.scal + SC_NRM, skip, s);
+}
+
 static int solve_core(const Dims& d, const Bufs& B, const double* L64, const float* X32, int mode,
-                      int refine_iters, const int* skip, cudaStream_t s) {
+                      int refine_iters, const int* skip, cudaStream_t s, bool rhs_ready = false) {
   const int64_t n = d.ncore;
   double* nrm = B.scal + SC_NRM;
-  // b = S^T (K w), ||b||^2, and K w kept for the last line
-  CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.w, 1, nullptr, nullptr, B.b, B.Kw, nrm, skip, s));
+  if (!rhs_ready) CP_TRY(core_rhs(d, B, skip, s));
   if (mode == CP_CORE_F64) {
     CP_CUDA(cudaMemcpyAsync(B.res, B.b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CP_TRY((chol_solve<double, double>(L64, n, B.res, B.dcor, B.y, skip, s)));
@@ -414,6 +419,8 @@ struct cp_state {
   Layout L;
   Bufs B;
   cudaStream_t side = nullptr;           // second stream for the pivot chain of the core inversion
+  cudaStream_t rhs = nullptr;            // third stream: the core system's right-hand side
+  cudaEvent_t ev_rhs_fork = nullptr, ev_rhs_join = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -503,6 +510,9 @@ extern "C" int cp_state_create(const cp_shape* shape, const cp_opts* opts, doubl
   st->B = carve(L, ws, d.ncore);
   if (opts->core_mode == CP_CORE_MIXED) {
     if (cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st->rhs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&st->ev_rhs_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&st->ev_rhs_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming) != cudaSuccess) {
       cp_state_destroy(st);
@@ -519,6 +529,9 @@ extern "C" int cp_state_destroy(cp_state* st) {
     if (st->ev_fork) cudaEventDestroy(st->ev_fork);
     if (st->ev_join) cudaEventDestroy(st->ev_join);
     if (st->side) cudaStreamDestroy(st->side);
+    if (st->rhs) cudaStreamDestroy(st->rhs);
+    if (st->ev_rhs_fork) cudaEventDestroy(st->ev_rhs_fork);
+    if (st->ev_rhs_join) cudaEventDestroy(st->ev_rhs_join);
   }
   delete st;
   return CP_OK;
@@ -574,12 +587,19 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
     CP_TRY(chol_factor<double>(B.core64, d.ncore, B.info + IN_INFO, skip, s));
     CP_TRY(solve_core(d, B, B.core64, nullptr, CP_CORE_F64, 0, skip, s));
   } else {
+    // the right-hand side runs on a third stream while the core is filled and
+    // inverted (the inversion's pivot chain leaves most SMs idle)
+    CP_CUDA(cudaEventRecord(st->ev_rhs_fork, s));
+    CP_CUDA(cudaStreamWaitEvent(st->rhs, st->ev_rhs_fork, 0));
+    CP_TRY(core_rhs(d, B, skip, st->rhs));
+    CP_CUDA(cudaEventRecord(st->ev_rhs_join, st->rhs));
     CP_TRY(launch_core_fill<float>(d, B.LC, B.U, B.Wp, B.core32, 1, skip, s));
     float* inv = nullptr;
     // the core's first R^2 x R^2 diagonal block is the identity
     CP_TRY(gj_invert<float>(B.core32, B.core32b, B.pinv, d.ncore, d.RR, B.info + IN_INFO, skip, s, st->side,
                             st->ev_fork, st->ev_join, &inv));
-    CP_TRY(solve_core(d, B, nullptr, inv, CP_CORE_MIXED, st->o.refine_iters, skip, s));
+    CP_CUDA(cudaStreamWaitEvent(s, st->ev_rhs_join, 0));
+    CP_TRY(solve_core(d, B, nullptr, inv, CP_CORE_MIXED, st->o.refine_iters, skip, s, true));
   }
   const int64_t nupd = update_ctas(d);
   k_update<<<unsigned(nupd), kUpdRows * 32, 0, s>>>(d, st->a, B.m, B.Gnm, B.Gt, B.f, mu, B.delta, B.at,
