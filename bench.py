@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="length of the served Poisson stream (0 = skip)")
     p.add_argument("--serve-rate", type=float, default=200.0)
+    p.add_argument("--serve-slots", type=int, default=4,
+                   help="large requests running at once on their own device States")
     p.add_argument("--no-extras", action="store_true",
                    help="only the timed steps (no float64 form, time-to-fit, oracle)")
     p.add_argument("--profile", default="", choices=["", "mttkrp", "step"],
@@ -571,7 +573,7 @@ def _run_ours(args, rank, world, local):
         if not args.no_batch:
             out["batched"] = bench_batched(seed)
         if args.serve_seconds > 0:
-            out["served"] = bench_served(seed, args.serve_seconds, args.serve_rate)
+            out["served"] = bench_served(seed, args.serve_seconds, args.serve_rate, args.serve_slots)
 
         # --- CPU oracle on the host cores (bounded sample) ---
         rate, iters, secs = oracle_rate(prob, args.cpu_seconds)
@@ -659,7 +661,7 @@ def bench_batched(seed):
             "time_to_fit_gain": per64 * 512 / t}
 
 
-def bench_served(seed, seconds, rate):
+def bench_served(seed, seconds, rate, slots=4):
     """Poisson request stream (70 % 32^3 R=5, 25 % 128^3 R=16, 5 % 400^3
     R=30; float32 tensors; stop at relative error change < 1e-8) served by
     the continuous-batching loop in real time."""
@@ -667,7 +669,7 @@ def bench_served(seed, seconds, rate):
     from paper_1205_2584_gb300 import serve as S
     from paper_1205_2584_gb300 import cpdgn as cp
     budget = 64 << 30
-    srv = S.Server(hbm_budget=budget, arena_bytes=8 << 30, large_slots=4, tol=1e-8, max_iter=1000)
+    srv = S.Server(hbm_budget=budget, arena_bytes=8 << 30, large_slots=slots, tol=1e-8, max_iter=1000)
     classes = [((32, 32, 32), 5), ((128, 128, 128), 16), ((400, 400, 400), 30)]
     warm = [S.Request(rid=-1 - k, arrival=0.0, dims=d, R=R, seed=12345 + k, collinearity=0.5)
             for k, (d, R) in enumerate(classes)]
@@ -680,6 +682,7 @@ def bench_served(seed, seconds, rate):
                        f"5% 400^3 R30, collinearity U[0,0.95], snr30, f32",
            "offered": len(reqs), **S.summarize(res, wall), "wall_s": wall,
            "hbm_budget_gb": budget / 2 ** 30, "peak_admitted_gb": srv.peak_bytes / 2 ** 30,
+           "large_slots": slots,
            "lane_rounds": [ln.rounds for ln in srv.lanes], "state_rounds": srv.large_rounds}
     # the same request alone, mixed form vs plain float64 form, per class
     alone = {}

@@ -40,8 +40,10 @@ def general_spd(n, seed):
     return (B @ B.T / n + 0.05 * np.eye(n)).astype(np.float32)
 
 
+# large cores (the 400^3, R = 30 core is n = 2700) and n % 4 != 0 (scalar operand loads)
 @pytest.mark.parametrize("n,block,ident", [(1200, 400, 400), (900, 225, 225), (75, 25, 25), (130, 0, 0),
-                                           (64, 0, 0), (50, 0, 0), (257, 0, 0)])
+                                           (64, 0, 0), (50, 0, 0), (257, 0, 0), (2700, 900, 900),
+                                           (1600, 0, 0), (1537, 0, 0)])
 def test_inverse_matches_float64(cp, n, block, ident):
     M = spd_with_identity_blocks(n, block, 7 + n) if block else general_spd(n, 7 + n)
     ref = np.linalg.inv(M.astype(np.float64))
