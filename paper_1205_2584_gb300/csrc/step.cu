@@ -7,8 +7,12 @@
 //   k_gram_cp/_had    C^(n), P^(n) = A^(n)T M_n, Gamma^(n,m), Gamma
 //   k_mode_prep       Gt^(n), U_n, L_n, w                 (Algorithm 1 steps 5-7)
 //   k_core_w/_fill    core = I + S^T K S                   (step 8-9, SPD form)
-//   chol_factor       core = L L^T (float64, or float32 in the mixed mode)
-//   solve             f = K w - K S core^{-1} S^T K w      (step 9)
+//   chol_factor       core = L L^T (float64 form), or
+//   gj_invert         core^{-1} in float32 (mixed form; Gauss-Jordan, the
+//                     pivot chain on a second stream; meanwhile a third
+//                     stream forms b = S^T K w)
+//   solve             f = K w - K S core^{-1} S^T K w      (step 9): triangular
+//                     solves, or float64 refinement sweeps with the inverse
 //   k_update          Delta A^(n) = (G_n - A^(n) F_n) Gt^(n), trial factors,
 //                     Delta^T (g + mu Delta) and column norms (steps 10-11)
 //   mttkrp            M_n and ||E||^2 at the trial factors (one pass over Y)
