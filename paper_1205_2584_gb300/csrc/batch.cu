@@ -368,12 +368,27 @@ __device__ void b_core(const BCtx& c) {
 }
 
 // In-CTA blocked right-looking Cholesky of the float32 core (lower, in global
-// memory).  Returns false on a non-positive or non-finite pivot.
+// memory).  Returns false on a non-positive or non-finite pivot.  The solved
+// panel of each block step (rows below the diagonal block) is also kept in
+// shared memory -- in the pass buffers Af and Mn, unused during the
+// factorisation -- so the trailing update reads its operands there instead
+// of from global memory; rows beyond that space (cores above about 770) keep
+// reading global memory.
+// Panel rows are BNB + 1 floats apart: the threads of a warp read rows two
+// apart at the same k, and a pitch of 33 puts them in different banks.
+constexpr int kPanPitch = BNB + 1;
+template <int TF>
+__device__ __forceinline__ float* b_panel_row(BShared<TF>& sh, int r) {
+  constexpr int cap = int(sizeof(sh.Af) / sizeof(float)) / kPanPitch;
+  return r < cap ? sh.Af + r * kPanPitch : sh.Mn + (r - cap) * kPanPitch;
+}
 template <int TF>
 __device__ bool b_chol(const BCtx& c, BShared<TF>& sh) {
   const int n = c.n, tid = threadIdx.x;
   float* A = c.core;
   constexpr int L = BNB + 1;
+  constexpr int kPanRows = int(sizeof(sh.Af) / sizeof(float)) / kPanPitch +
+                           int(sizeof(sh.Mn) / sizeof(float)) / kPanPitch;
   if (tid == 0) sh.flags[1] = 1;
   for (int k0 = 0; k0 < n; k0 += BNB) {
     const int kb = (n - k0) < BNB ? (n - k0) : BNB;
@@ -421,9 +436,16 @@ __device__ bool b_chol(const BCtx& c, BShared<TF>& sh) {
 #pragma unroll
       for (int j = 0; j < BNB; ++j)
         if (j < kb) A[r + int64_t(n) * (k0 + j)] = x[j];
+      const int pr = r - (k0 + kb);
+      if (pr < kPanRows) {
+        float* dst = b_panel_row(sh, pr);
+#pragma unroll
+        for (int j = 0; j < BNB; ++j) dst[j] = (j < kb) ? x[j] : 0.f;
+      }
     }
     __syncthreads();
-    // trailing update of the lower triangle, 2 x 2 blocks per thread
+    // trailing update of the lower triangle, 2 x 2 blocks per thread, the
+    // panel read from shared memory (global memory past kPanRows rows)
     const int m0 = k0 + kb, rest = n - m0;
     const int nb2 = (rest + 1) / 2;
     for (int64_t e = tid; e < int64_t(nb2) * nb2; e += BT) {
@@ -432,14 +454,29 @@ __device__ bool b_chol(const BCtx& c, BShared<TF>& sh) {
       const int i0 = m0 + 2 * bi, j0 = m0 + 2 * bj;
       float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
       const bool i1ok = i0 + 1 < n, j1ok = j0 + 1 < n;
-      for (int q = 0; q < kb; ++q) {
-        const float* col = A + int64_t(n) * (k0 + q);
-        const float a0 = col[i0], a1 = i1ok ? col[i0 + 1] : 0.f;
-        const float b0 = col[j0], b1 = j1ok ? col[j0 + 1] : 0.f;
-        c00 = fmaf(a0, b0, c00);
-        c01 = fmaf(a0, b1, c01);
-        c10 = fmaf(a1, b0, c10);
-        c11 = fmaf(a1, b1, c11);
+      if (i0 + 1 - m0 < kPanRows) {      // i0 >= j0, so every row needed is staged
+        const float* pa0 = b_panel_row(sh, i0 - m0);
+        const float* pa1 = b_panel_row(sh, i0 + 1 - m0);
+        const float* pb0 = b_panel_row(sh, j0 - m0);
+        const float* pb1 = b_panel_row(sh, j0 + 1 - m0);
+        for (int q = 0; q < kb; ++q) {
+          const float a0 = pa0[q], a1 = i1ok ? pa1[q] : 0.f;
+          const float b0 = pb0[q], b1 = j1ok ? pb1[q] : 0.f;
+          c00 = fmaf(a0, b0, c00);
+          c01 = fmaf(a0, b1, c01);
+          c10 = fmaf(a1, b0, c10);
+          c11 = fmaf(a1, b1, c11);
+        }
+      } else {
+        for (int q = 0; q < kb; ++q) {
+          const float* col = A + int64_t(n) * (k0 + q);
+          const float a0 = col[i0], a1 = i1ok ? col[i0 + 1] : 0.f;
+          const float b0 = col[j0], b1 = j1ok ? col[j0 + 1] : 0.f;
+          c00 = fmaf(a0, b0, c00);
+          c01 = fmaf(a0, b1, c01);
+          c10 = fmaf(a1, b0, c10);
+          c11 = fmaf(a1, b1, c11);
+        }
       }
       A[i0 + int64_t(n) * j0] -= c00;
       if (j1ok && j0 + 1 <= i0) A[i0 + int64_t(n) * (j0 + 1)] -= c01;
