@@ -658,32 +658,75 @@ __device__ double b_solve(const BCtx& c, BShared<TF>& sh, int refine_iters) {
 template <int TF>
 __device__ double b_update(const BCtx& c, BShared<TF>& sh, double mu) {
   const int R = c.R, RR = c.RR, N = c.N;
+  // Gamma^(n) + F_n and Gamma^(n) rounded to float32 once per mode, in the
+  // pass buffer Mn (unused between passes); float64 -> float32 conversions
+  // run on this part's slow float64 pipe, so none is repeated per row
+  float* gf = sh.Mn;
+  float* gg = sh.Mn + N * RR;
+  for (int e = threadIdx.x; e < N * RR; e += BT) {
+    const int n = e / RR, q = e % RR;
+    const double gm = c.Gnm[(int64_t(n) * N + n) * RR + q];
+    gf[e] = float(gm + c.f[int64_t(n) * RR + q]);
+    gg[e] = float(gm);
+  }
+  __syncthreads();
   double den = 0.0;
-  for (int64_t e = threadIdx.x; e < c.T * R; e += BT) {
+  // The gain-ratio denominator sum_e Delta_e (g_e + mu Delta_e) is added in
+  // the entry order e = tid, tid + BT, ... (then the fixed tree of bsum), so
+  // that it does not depend on how entries are assigned to threads below:
+  // the factors' trajectory, and so each problem's trial count, stays that of
+  // the entry-per-thread form.  q_e = g_e + mu Delta_e waits in the pass
+  // buffer Af when the T R entries fit.
+  double* qs = reinterpret_cast<double*>(sh.Af);
+  const bool replay = c.T * R <= int64_t(sizeof(sh.Af) / sizeof(double));
+  // one factor row (mode n, index i) per thread: h[s] = (M - A Gamma - A F)[i, s]
+  // and g[s] = (M - A Gamma)[i, s] once, then Delta[i, r] = h Gt[:, r]
+  for (int64_t row = threadIdx.x; row < c.T; row += BT) {
     int n = 0;
-    while (n + 1 < N && e >= c.aoff[n + 1]) ++n;
+    while (n + 1 < N && row >= c.aoff[n + 1] / R) ++n;
     const int64_t In = c.I[n];
-    const int64_t loc = e - c.aoff[n];
-    const int i = int(loc % In), r = int(loc / In);
+    const int i = int(row - c.aoff[n] / R);
     const double* An = c.a + c.aoff[n];
-    const double* Gm = c.Gnm + (int64_t(n) * N + n) * RR;
-    const double* Fn = c.f + int64_t(n) * RR;
+    const double* Mn = c.M + c.aoff[n];
     const double* Gtn = c.Gt + int64_t(n) * RR;
-    // h[s] = (M - A Gamma - A F)[i, s] for all s, then dl = h Gt[:, r]
-    double dl = 0.0, g = 0.0;
-    for (int s2 = 0; s2 < R; ++s2) {
-      float t1 = 0.f;
-      for (int k = 0; k < R; ++k) t1 = fmaf(float(An[i + In * k]), float(Gm[k + R * s2] + Fn[k + R * s2]), t1);
-      float t2 = 0.f;
-      for (int k = 0; k < R; ++k) t2 = fmaf(float(An[i + In * k]), float(Gm[k + R * s2]), t2);
-      const double Ms = c.M[c.aoff[n] + i + In * s2];
-      const double h = Ms - double(t1);
-      dl = fma(h, Gtn[s2 + R * r], dl);
-      if (s2 == r) g = Ms - double(t2);
+    const float* gfn = gf + n * RR;
+    const float* ggn = gg + n * RR;
+    float ar[BR];
+#pragma unroll
+    for (int k = 0; k < BR; ++k) ar[k] = (k < R) ? float(An[i + In * k]) : 0.f;
+    double h[BR], g[BR];
+#pragma unroll
+    for (int s2 = 0; s2 < BR; ++s2) {
+      if (s2 < R) {
+        float t1 = 0.f, t2 = 0.f;
+        for (int k = 0; k < R; ++k) {
+          t1 = fmaf(ar[k], gfn[k + R * s2], t1);
+          t2 = fmaf(ar[k], ggn[k + R * s2], t2);
+        }
+        const double Ms = Mn[i + In * s2];
+        h[s2] = Ms - double(t1);
+        g[s2] = Ms - double(t2);
+      }
     }
-    den = fma(dl, g + mu * dl, den);
-    c.delta[e] = dl;
-    c.At[e] = An[i + In * r] + dl;
+    for (int r = 0; r < R; ++r) {
+      double dl = 0.0;
+#pragma unroll
+      for (int s2 = 0; s2 < BR; ++s2)
+        if (s2 < R) dl = fma(h[s2], Gtn[s2 + R * r], dl);
+      double gr = 0.0;
+#pragma unroll
+      for (int s2 = 0; s2 < BR; ++s2)
+        if (s2 == r) gr = g[s2];
+      const int64_t e = c.aoff[n] + i + In * r;
+      if (replay) qs[e] = gr + mu * dl;
+      else den = fma(dl, gr + mu * dl, den);
+      c.delta[e] = dl;
+      c.At[e] = An[i + In * r] + dl;
+    }
+  }
+  if (replay) {
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < c.T * R; e += BT) den = fma(c.delta[e], qs[e], den);
   }
   const double dsum = bsum(den, sh.red);   // (ends with a barrier: At is complete)
   for (int e = threadIdx.x; e < N * R; e += BT) {   // column norms^2 in row order
