@@ -328,35 +328,89 @@ __device__ __forceinline__ void bpair(int p, int* n, int* m) {
 }
 
 // core = I + S^T K S, lower triangle, float32 (n x n, ld n)
-__device__ void b_core(const BCtx& c) {
+template <int TF>
+__device__ void b_core(const BCtx& c, BShared<TF>& sh) {
   const int R = c.R, RR = c.RR, N = c.N, n = c.n;
   const int npairs = N * (N - 1) / 2;
   const int R3 = RR * R;
-  for (int e = threadIdx.x; e < npairs * R3; e += BT) {
-    const int p = e / R3, q = e % R3, aa = q % R, k = (q / R) % R, j = q / RR;
-    int nn, m;
-    bpair(p, &nn, &m);
-    const double* G = c.Gnm + (int64_t(nn) * N + m) * RR;
-    const double* Lm = c.LC + int64_t(m) * RR;
-    const double* Un = c.U + int64_t(nn) * RR;
-    float s = 0.f;
-    for (int bb = k; bb <= j; ++bb) s = fmaf(float(G[aa + R * bb]), float(Lm[bb + R * k] * Un[bb + R * j]), s);
-    c.Wp[e] = s;
-  }
-  __syncthreads();
-  for (int64_t e = threadIdx.x; e < int64_t(npairs) * RR * RR; e += BT) {
-    const int p = int(e / (int64_t(RR) * RR));
-    const int q = int(e % (int64_t(RR) * RR));
-    const int rho = q % RR, kap = q / RR;
-    int nn, m;
-    bpair(p, &nn, &m);
-    const int i = rho % R, j = rho / R, k = kap % R, l = kap / R;
-    const double* Ln = c.LC + int64_t(nn) * RR;
-    const double* Um = c.U + int64_t(m) * RR;
-    const double* W = c.Wp + int64_t(p) * R3;
-    float s = 0.f;
-    for (int aa = i; aa <= l; ++aa) s = fmaf(float(Ln[aa + R * i] * Um[aa + R * l]), float(W[aa + R * (k + R * j)]), s);
-    c.core[(int64_t(nn) * RR + rho) + int64_t(n) * (int64_t(m) * RR + kap)] = s;
+  // Fast path: the float32 roundings the sums below take of float64 products
+  // and values -- float(L_m[b,k] U_n[b,j]), float(Gamma^(n,m)), and for the
+  // core blocks float(L_n[a,i] U_m[a,l]) -- are formed once per block pair in
+  // the pass buffers (Af, Mn: unused here) instead of once per term (each a
+  // float64 multiply and conversions on this part's slow float64 pipe), and
+  // W stays in shared memory.  Same values, same order: results are those of
+  // the per-term form below, which remains for shapes whose tables do not fit.
+  const bool fast = 2 * npairs * R3 <= int(sizeof(sh.Af) / sizeof(float)) &&
+                    npairs * (R3 + RR) <= int(sizeof(sh.Mn) / sizeof(float));
+  if (fast) {
+    float* P = sh.Af;                         // P[p][a][i][l] = float(L_n[a,i] U_m[a,l])
+    float* W = sh.Af + npairs * R3;           // W[p][a + R (k + R j)]
+    float* Q = sh.Mn;                         // Q[p][b][k][j] = float(L_m[b,k] U_n[b,j])
+    float* Gf = sh.Mn + npairs * R3;          // Gf[p][a + R b] = float(Gamma^(n,m)[a,b])
+    for (int e = threadIdx.x; e < npairs * R3; e += BT) {
+      const int p = e / R3, q = e % R3, x = q / RR, y = (q / R) % R, z = q % R;
+      int nn, m;
+      bpair(p, &nn, &m);
+      // P: (a, i, l) = (x, y, z); Q: (b, k, j) = (x, y, z)
+      P[e] = float(c.LC[int64_t(nn) * RR + x + R * y] * c.U[int64_t(m) * RR + x + R * z]);
+      Q[e] = float(c.LC[int64_t(m) * RR + x + R * y] * c.U[int64_t(nn) * RR + x + R * z]);
+    }
+    for (int e = threadIdx.x; e < npairs * RR; e += BT) {
+      const int p = e / RR, q = e % RR;
+      int nn, m;
+      bpair(p, &nn, &m);
+      Gf[e] = float(c.Gnm[(int64_t(nn) * N + m) * RR + q]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < npairs * R3; e += BT) {
+      const int p = e / R3, q = e % R3, aa = q % R, k = (q / R) % R, j = q / RR;
+      const float* Qp = Q + p * R3;
+      const float* Gp = Gf + p * RR;
+      float s = 0.f;
+      for (int bb = k; bb <= j; ++bb) s = fmaf(Gp[aa + R * bb], Qp[bb * RR + k * R + j], s);
+      W[e] = s;
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < int64_t(npairs) * RR * RR; e += BT) {
+      const int p = int(e / (int64_t(RR) * RR));
+      const int q = int(e % (int64_t(RR) * RR));
+      const int rho = q % RR, kap = q / RR;
+      int nn, m;
+      bpair(p, &nn, &m);
+      const int i = rho % R, j = rho / R, k = kap % R, l = kap / R;
+      const float* Pp = P + p * R3;
+      const float* Wq = W + p * R3;
+      float s = 0.f;
+      for (int aa = i; aa <= l; ++aa) s = fmaf(Pp[aa * RR + i * R + l], Wq[aa + R * (k + R * j)], s);
+      c.core[(int64_t(nn) * RR + rho) + int64_t(n) * (int64_t(m) * RR + kap)] = s;
+    }
+  } else {
+    for (int e = threadIdx.x; e < npairs * R3; e += BT) {
+      const int p = e / R3, q = e % R3, aa = q % R, k = (q / R) % R, j = q / RR;
+      int nn, m;
+      bpair(p, &nn, &m);
+      const double* G = c.Gnm + (int64_t(nn) * N + m) * RR;
+      const double* Lm = c.LC + int64_t(m) * RR;
+      const double* Un = c.U + int64_t(nn) * RR;
+      float s = 0.f;
+      for (int bb = k; bb <= j; ++bb) s = fmaf(float(G[aa + R * bb]), float(Lm[bb + R * k] * Un[bb + R * j]), s);
+      c.Wp[e] = s;
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < int64_t(npairs) * RR * RR; e += BT) {
+      const int p = int(e / (int64_t(RR) * RR));
+      const int q = int(e % (int64_t(RR) * RR));
+      const int rho = q % RR, kap = q / RR;
+      int nn, m;
+      bpair(p, &nn, &m);
+      const int i = rho % R, j = rho / R, k = kap % R, l = kap / R;
+      const double* Ln = c.LC + int64_t(nn) * RR;
+      const double* Um = c.U + int64_t(m) * RR;
+      const double* W = c.Wp + int64_t(p) * R3;
+      float s = 0.f;
+      for (int aa = i; aa <= l; ++aa) s = fmaf(float(Ln[aa + R * i] * Um[aa + R * l]), float(W[aa + R * (k + R * j)]), s);
+      c.core[(int64_t(nn) * RR + rho) + int64_t(n) * (int64_t(m) * RR + kap)] = s;
+    }
   }
   for (int64_t e = threadIdx.x; e < int64_t(N) * RR * RR; e += BT) {
     const int nn = int(e / (int64_t(RR) * RR));
@@ -836,7 +890,7 @@ __global__ void __launch_bounds__(BT) k_batch_lm(const cp_batch_problem* probs, 
       const double mu = st->mu;
       b_gram(c, sh, c.a, c.M);
       bool ok = b_mode_prep(c, sh, mu);
-      b_core(c);
+      b_core(c, sh);
       ok = b_chol(c, sh) && ok;
       const double rel = b_solve(c, sh, o.refine_iters);
       const double den = b_update(c, sh, mu);
