@@ -1,0 +1,7 @@
+// The batched kernel for tensor tiles of 32 fibres.
+#include "batch_kernel.cuh"
+
+namespace cpdgn {
+template int batch_launch<32>(const cp_batch_problem*, int, const float*, double*, void*, cp_status*,
+                                const cp_opts*, int, int, const int*, cudaStream_t);
+}  // namespace cpdgn
