@@ -66,7 +66,7 @@ __device__ __forceinline__ void b_cp_async4(float* dst, const float* src) {
 __device__ __forceinline__ void b_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void b_cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-__device__ double bsum(double v, double* red) {
+static __device__ double bsum(double v, double* red) {
   __syncthreads();
   red[threadIdx.x] = v;
   __syncthreads();
