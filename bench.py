@@ -47,8 +47,8 @@ WORKLOAD = "cp3-200^3-R20-collinear(0.95,0.81,0.81)-snr40"
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_mttkrp_tc3 launch, from
 # the ncu captures summarised in profiles/k_mttkrp_tc3_bf16x2.md (bytes)
-TRAFFIC_200 = 32.293376e6
-TRAFFIC_512 = 537.939712e6 + 3.137536e6
+TRAFFIC_200 = 32.299520e6
+TRAFFIC_512 = 537.898752e6 + 2.792192e6
 # dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one core
 # inverse (n = 1200), from the ncu capture summarised in
 # profiles/k_gj_inverse_traffic.md (bytes; every kernel with cold caches under ncu)
