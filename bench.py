@@ -499,6 +499,24 @@ def _run_ours(args, rank, world, local):
                                   "mttkrp_ms": time_pass(shape32, Y32, cp.factors_to_device(prob32.init))}
         st32.close()
 
+        # --- ALS sweeps (Sec. 3, Eq. ALS; the initialisation before fLM) on the
+        # same two-plane tensor: N passes over Y per sweep, one per mode ---
+        st_a, a_a = new_state(shape2, cp.CP_CORE_MIXED, prob.init)
+        st_a.init(Y2)
+        st_a.als(Y2, 2)
+        torch.cuda.synchronize()
+        ka = 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st_a.als(Y2, ka)
+        e1.record()
+        torch.cuda.synchronize()
+        als_ms = e0.elapsed_time(e1) / ka
+        out["als"] = {"value": 1e3 / als_ms, "unit": "sweeps/s", "ms_per_sweep": als_ms,
+                      "passes_per_sweep": len(DIMS), "sweeps_timed": ka,
+                      "status_error": st_a.status()["error"]}
+        st_a.close()
+
         # --- end to end through the public API: float32 tensor on the host ---
         # Every step copies its own input (the pinned float32 tensor) to the
         # device, splits it into the two-plane form, runs the step (one replay

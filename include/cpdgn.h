@@ -279,6 +279,22 @@ int cp_state_graph_kernels(cp_state* st);
 /* Device address of the state's cp_status (inside ws). */
 cp_status* cp_state_status(cp_state* st);
 
+/* `sweeps` (>= 1) sweeps of the ALS rule (Sec. 3, Eq. ALS), the
+ * initialisation the paper runs before fLM (Sec. 4.6): for n = 1..N in turn,
+ *   A^(n) <- Y_(n) (A^(N) (.) ... A^(n+1) (.) A^(n-1) (.) ... A^(1)) (Gamma^(n))^{-1},
+ *   Gamma^(n) = Hadamard_{k != n} C^(k),
+ * with the MTTKRP from a pass over Y at the current factors (earlier modes of
+ * the sweep already replaced) and Gamma^(n) factored by Cholesky (the rule's
+ * pseudo-inverse is this inverse when the other factors have full column
+ * rank).  The state's factor buffer `a` is updated in place.  The damping,
+ * the counters and the cached MTTKRP of the LM iteration are not maintained:
+ * call cp_state_init before the next cp_dgn_step.  If Gamma^(n) is not
+ * positive definite, mode n keeps its factor and the status records
+ * error = CP_ENOTSPD and info = the failing pivot (1-based), unless it holds
+ * an error already.  Asynchronous on `stream`, no host synchronisation
+ * (graph-capturable); CP_EINVAL for a NULL state or tensor or sweeps < 1. */
+int cp_als_sweep(cp_state* st, const void* Y, int sweeps, void* stream);
+
 /* Device address of an intermediate of the last trial, for inspection:
  * 0 = m (MTTKRP at the current factors, R*T), 1 = delta (last step, R*T),
  * 2 = Gt (N R x R), 3 = w (N R^2), 4 = f (N R^2), 5 = a_trial (R*T).

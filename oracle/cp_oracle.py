@@ -478,3 +478,21 @@ def lm_fit(Y, A0, mu0: Optional[float] = None, max_iter: int = 200, tol: float =
             break
     return LMResult(A=A, resid2=r2, rel_err=math.sqrt(r2) / ynorm, iters=it,
                     accepted=accepted, mu=mu, stop=stop, history=hist)
+
+
+# ---------------------------------------------------------------------------
+# ALS (Sec. 3, Eq. ALS): the initialisation sweeps run before fLM (Sec. 4.6)
+# ---------------------------------------------------------------------------
+
+
+def als_sweep(Y: np.ndarray, A: Sequence[np.ndarray],
+              modes: Optional[Sequence[int]] = None) -> List[np.ndarray]:
+    """One sweep of the ALS rule: for n in ``modes`` (every mode, in order, by
+    default) A^(n) <- Y_(n) KR_n (Gamma^(n))^+, with Gamma^(n) = Hadamard_{k != n}
+    C^(k) formed from the current factors (modes earlier in the sweep already
+    replaced).  The pseudo-inverse is the one the rule prints; it is the
+    inverse whenever the other factors have full column rank."""
+    A = [np.array(a, dtype=np.float64, copy=True) for a in A]
+    for n in (range(len(A)) if modes is None else modes):
+        A[n] = mttkrp(Y, A, n) @ np.linalg.pinv(grams(A).Gamma(n))
+    return A

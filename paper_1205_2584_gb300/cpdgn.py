@@ -80,6 +80,7 @@ _sig = {
     "cp_dgn_step": [_vp, _vp, _vp],
     "cp_state_capture": [_vp, _vp, ctypes.c_int, _vp],
     "cp_state_launch": [_vp, _vp],
+    "cp_als_sweep": [_vp, _vp, ctypes.c_int, _vp],
     "cp_state_graph_kernels": [_vp],
     "cp_batch_run": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                      ctypes.c_int, _vp, _vp],
@@ -299,6 +300,11 @@ class State:
 
     def launch(self, stream=None):
         _check(_lib.cp_state_launch(self._h, _stream(stream)), "cp_state_launch")
+
+    def als(self, Y: torch.Tensor, sweeps: int = 1, stream=None):
+        """`sweeps` ALS sweeps on the factors (cp_als_sweep); call init(Y)
+        before the next step."""
+        _check(_lib.cp_als_sweep(self._h, _ptr(Y), int(sweeps), _stream(stream)), "cp_als_sweep")
 
     @property
     def graph_kernels(self) -> int:

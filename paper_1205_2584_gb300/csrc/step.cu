@@ -543,6 +543,89 @@ extern "C" int cp_state_destroy(cp_state* st) {
 
 extern "C" cp_status* cp_state_status(cp_state* st) { return st ? st->B.status : nullptr; }
 
+// ---------------------------------------------------------------------------
+// ALS sweeps (Sec. 3, Eq. ALS) on a state's factors: for n = 1..N in turn,
+// A^(n) <- M_n (Gamma^(n))^{-1} with M_n from a pass over Y at the current
+// factors and Gamma^(n) = Hadamard_{k != n} C^(k) from their Gramians.
+// ---------------------------------------------------------------------------
+namespace cpdgn {
+
+constexpr int kAlsThreads = 128;
+
+// Rows of A^(n) = M_n Gamma^{-1}.  Every CTA factors Gamma = L L^T (at most
+// 32 x 32; one warp, lane i owning row i) in shared memory, then each thread
+// solves x Gamma = m for one row by two triangular solves.  A non-positive or
+// non-finite pivot leaves A^(n) unchanged and records CP_ENOTSPD with the
+// pivot (1-based) in the status, unless an error is recorded already.
+__global__ void __launch_bounds__(kAlsThreads) k_als_mode(Dims d, int n, const double* G, const double* Mn,
+                                                         double* An, cp_status* st) {
+  __shared__ double L[CP_MAX_R * CP_MAX_R];
+  __shared__ int bad;
+  const int R = d.R, tid = threadIdx.x;
+  for (int e = tid; e < R * R; e += blockDim.x) L[e] = G[e];
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  if (tid < 32) {
+    for (int j = 0; j < R; ++j) {
+      if (tid == j) {
+        double p = L[j + R * j];
+        if (!(p > 0.0) || !isfinite(p)) {
+          if (bad == 0) bad = j + 1;
+          p = 1.0;
+        }
+        L[j + R * j] = sqrt(p);
+      }
+      __syncwarp();
+      if (tid > j && tid < R) L[tid + R * j] /= L[j + R * j];
+      __syncwarp();
+      if (tid > j && tid < R)
+        for (int k = j + 1; k <= tid; ++k) L[tid + R * k] = fma(-L[tid + R * j], L[k + R * j], L[tid + R * k]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (bad) {
+    if (blockIdx.x == 0 && tid == 0 && atomicCAS(&st->error, 0, CP_ENOTSPD) == 0) st->info = bad;
+    return;
+  }
+  const int64_t In = d.I[n];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + tid; i < In; i += int64_t(gridDim.x) * blockDim.x) {
+    double x[CP_MAX_R];
+    for (int r = 0; r < R; ++r) x[r] = Mn[i + In * r];
+    for (int r = 0; r < R; ++r) {                 // L y = m^T
+      double v = x[r];
+      for (int k = 0; k < r; ++k) v = fma(-L[r + R * k], x[k], v);
+      x[r] = v / L[r + R * r];
+    }
+    for (int r = R - 1; r >= 0; --r) {            // L^T x = y
+      double v = x[r];
+      for (int k = r + 1; k < R; ++k) v = fma(-L[k + R * r], x[k], v);
+      x[r] = v / L[r + R * r];
+    }
+    for (int r = 0; r < R; ++r) An[i + In * r] = x[r];
+  }
+}
+
+}  // namespace cpdgn
+
+extern "C" int cp_als_sweep(cp_state* st, const void* Y, int sweeps, void* stream) {
+  if (!st || !Y || sweeps < 1) return CP_EINVAL;
+  const Dims& d = st->d;
+  const Bufs& B = st->B;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int it = 0; it < sweeps; ++it)
+    for (int n = 0; n < d.N; ++n) {
+      CP_CUDA(cudaMemsetAsync(B.m, 0, size_t(d.T) * d.R * sizeof(double), s));
+      CP_TRY(launch_mttkrp(d, Y, st->a, B.m, nullptr, nullptr, s));
+      CP_TRY(launch_gram(d, st->a, nullptr, B.gpart, B.C, nullptr, B.Gnm, nullptr, nullptr, s));
+      int64_t g = (d.I[n] + kAlsThreads - 1) / kAlsThreads;
+      if (g > 4 * kSMs) g = 4 * kSMs;
+      k_als_mode<<<unsigned(g), kAlsThreads, 0, s>>>(d, n, B.Gnm + (int64_t(n) * d.N + n) * d.RR,
+                                                      B.m + d.aoff[n], st->a + d.aoff[n], B.status);
+    }
+  return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
+}
+
 extern "C" double* cp_state_buffer(cp_state* st, int id) {
   if (!st) return nullptr;
   switch (id) {
