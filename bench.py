@@ -17,9 +17,13 @@ trial of an unconverged run.  The 32 MB tensor fits in L2, so L2 is flushed (a
 
 Also reported: the plain float64 form (float64 tensor and float64 core
 Cholesky) on the same problem, time-to-fit of both forms (stop when an
-accepted step changes the relative error by < 1e-9), the MTTKRP pass alone
-against the measured HBM bandwidth, an end-to-end figure through the public
-API with host buffers, and the CPU oracle on the host cores.
+accepted step changes the relative error by < 1e-9), the float32 core
+inverse and the MTTKRP pass alone against their rooflines, an end-to-end
+figure through the public API (every step copies its float32 tensor from
+pinned host memory on a copy stream, overlapping the previous step, splits
+it and replays a captured one-step graph, then reads its status back), ALS
+sweeps on the same tensor, the batched and served forms, and the CPU oracle
+on the host cores.
 
 --impl reference times the CPU oracle (the float64 numpy implementation in
 oracle/) on the same workload instead.
