@@ -260,15 +260,17 @@ def gj_inverse_flops(n: int, ident: int, b: int = 64) -> int:
     matrix whose leading ident rows are the identity (eliminated at once):
     the identity step updates the (n - e)^2 trailing block with depth e;
     every later sweep with panel width w does the rank-w update of the n - w
-    rows outside the panel (all n columns), the row panel P^{-1} A[k, :]
-    and forms (two w^3 products) and inverts (w^3) its pivot block."""
+    rows outside the panel (all n columns), the row panel P^{-1} A[k, :] and
+    the inverse of its pivot block (w^3).  The library forms each next pivot
+    block ahead of its sweep; those products repeat work counted here (one
+    row-panel block and one update tile) and are not counted again."""
     nt = (n + b - 1) // b
     k0 = min(ident // b, nt - 1)
     e = k0 * b
     fma = (n - e) ** 2 * e
     for k in range(k0, nt):
         w = min(b, n - k * b)
-        fma += (n - w) * n * w + w * w * (n - w) + 3 * w ** 3
+        fma += (n - w) * n * w + w * w * (n - w) + w ** 3
     return 2 * fma
 
 
