@@ -49,13 +49,14 @@ DIMS = (200, 200, 200)
 R = 20
 WORKLOAD = "cp3-200^3-R20-collinear(0.95,0.81,0.81)-snr40"
 L2_FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_mttkrp_tc3 launch, from
-# the ncu captures summarised in profiles/k_mttkrp_tc3_bf16x2.md (bytes)
-TRAFFIC_200 = 32.299520e6
-TRAFFIC_512 = 537.898752e6 + 2.792192e6
-# dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one core
-# inverse (n = 1200), from the ncu capture summarised in
-# profiles/k_gj_inverse_traffic.md (bytes; every kernel with cold caches under ncu)
+# DRAM traffic per launch, dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture of the kernel (bytes); None where the kernel has changed
+# since its counters were taken.
+TRAFFIC_TC3_200 = 32.299520e6          # k_mttkrp_tc3, 200^3 R=20, two-plane tensor
+TRAFFIC_TC3_512 = 537.898752e6 + 2.792192e6   # k_mttkrp_tc3, 512^3 R=32
+TRAFFIC_TC_200 = None                  # k_mttkrp_tc, 200^3 R=20, float32 tensor
+# summed over the kernels of one float32 core inverse (n = 1200), every kernel
+# with cold caches under ncu (bytes)
 GJ_TRAFFIC = 88.605952e6
 # timed runs restart from their initial factors every this many launches
 RESTART_EVERY = 50
@@ -274,12 +275,23 @@ def gj_inverse_flops(n: int, ident: int, b: int = 64) -> int:
     return 2 * fma
 
 
+def core_cholesky_flops(N: int, R: int) -> float:
+    """The method's algorithmic core work per trial (Sec. 4.4 complexity):
+    one Cholesky of the N R^2 x N R^2 core, n^3 / 3 flops with n = N R^2."""
+    n = N * R * R
+    return n ** 3 / 3.0
+
+
 def core_inverse_roofline(cp, torch, flush, peaks, peak_src, seed, reps=20):
     """cp_spd_invert_f32 timed live on an SPD matrix shaped like the
     benchmark's core (n = N R^2 = 1200, identity diagonal R^2 x R^2 blocks),
     L2 flushed and the input restored between launches (outside the events).
     The call is captured once in a CUDA graph and the replays are timed, as
-    inside the step's graph (host launch overhead is not device time)."""
+    inside the step's graph (host launch overhead is not device time).
+
+    `achieved` counts the method's core work, one Cholesky of the core
+    (n^3 / 3 flops), over the time the library takes to solve the core system
+    this way; the inverse's own flop count is reported beside it."""
     import numpy as np
     n, blk = len(DIMS) * R * R, R * R
     rng = np.random.default_rng(seed + 17)
@@ -310,16 +322,21 @@ def core_inverse_roofline(cp, torch, flush, peaks, peak_src, seed, reps=20):
         evs.append((e0, e1))
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
-    flops = gj_inverse_flops(n, blk)
+    alg = core_cholesky_flops(len(DIMS), R)
+    own = gj_inverse_flops(n, blk)
     peak = GB300_SMS * FP32_FMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = flops / (ms * 1e-3) / 1e12
+    achieved = alg / (ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": "k_gj_* (float32 Gauss-Jordan inverse of the core, one call)",
             "workload": f"n = N R^2 = {n}, identity {blk} x {blk} blocks, SPD", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": GJ_TRAFFIC,
-            "ms_per_launch": ms, "algorithmic_flops": flops,
-            "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x max SM clock",
-            "note": "latency-bound pivot chain (13 sweeps of 64 dependent elimination steps); "
-                    "the tensor pass is reported in roofline_tensor_pass"}
+            "traffic_note": "DRAM bytes of one inverse under ncu, every kernel with cold caches: an upper "
+                            "bound; inside the step the core is L2-resident",
+            "ms_per_launch": ms, "algorithmic_flops": alg,
+            "algorithmic_count": "core Cholesky n^3/3, n = N R^2 (the method's core work, Sec. 4.4)",
+            "inverse_own_flops": own, "inverse_own_tflops": own / (ms * 1e-3) / 1e12,
+            "peak_source": "derived, not measured: 152 SMs x 128 FP32 FMA lanes x 2 flops x max SM clock "
+                           "(MEASURED_PEAKS.json has no FP32 figure)",
+            "note": "latency-bound pivot chain (13 sweeps of 64 dependent elimination steps)"}
 
 
 def oracle_rate_one_thread(seed: int, seconds: float):
@@ -367,19 +384,18 @@ def _run_ours(args, rank, world, local):
 
     seed = args.seed + rank
     peaks, peak_src = measured_peaks()
-    # the tensor is stored as two bfloat16 planes (hi + lo, 16 significant
-    # bits) that the tensor-core pass reads directly; the oracle and the
-    # float64 form see the same values
-    prob = synth.config2(seed, DIMS, dtype="bf16x2")
-    shape2 = cp.make_shape(DIMS, R, "bf16x2")
-    stream = torch.cuda.current_stream()
-    Y2 = cp.tensor_to_device(prob.Y, "bf16x2")
+    # the benchmark tensor: float32 values (config 2's "FP32" tensor); the
+    # oracle and the float64 form see the same values in float64
+    prob = synth.config2(seed, DIMS, dtype="f32")
+    shape32 = cp.make_shape(DIMS, R, "f32")
+    Y32 = cp.tensor_to_device(prob.Y, "f32")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def new_state(shape, mode, a0, tol=0.0, max_iter=10 ** 9, mu_max=float("inf")):
+    def new_state(shape, mode, a0, tol=0.0, max_iter=10 ** 9, mu_max=float("inf"), mu0=-1.0,
+                  normalize=True):
         a = cp.factors_to_device(a0)
-        st = cp.State(shape, a, mu0=-1.0, tau=1e-3, tol=tol, mu_max=mu_max, max_iter=max_iter,
-                      core_mode=mode, refine_iters=8)
+        st = cp.State(shape, a, mu0=mu0, tau=1e-3, tol=tol, mu_max=mu_max, max_iter=max_iter,
+                      core_mode=mode, refine_iters=8, normalize=normalize)
         return st, a
 
     def timed_steps(st, a, Y, K, W, period=RESTART_EVERY):
@@ -445,21 +461,23 @@ def _run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
 
-    # --- timed region: mixed form (tensor-core pass, float32 core factor) ---
-    st, a = new_state(shape2, cp.CP_CORE_MIXED, prob.init)
-    st.init(Y2)
+    # --- timed region: mixed form on the float32 tensor (tensor-core pass,
+    # float32 core inverse + float64 refinement, float64 control) ---
+    st, a = new_state(shape32, cp.CP_CORE_MIXED, prob.init)
+    st.init(Y32)
     with ClockSampler(local) as clk:
-        t_ms, nk = timed_steps(st, a, Y2, args.steps, args.warmup)
+        t_ms, nk = timed_steps(st, a, Y32, args.steps, args.warmup)
     status = st.status()
     value, ms_per_step, t_ms = aggregate(t_ms, args.steps, world)
 
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "bf16 tensor-core operands (f32 accumulate), f32 core factor, f64 control",
+           "dtype": "f32 tensor (bf16-piece tensor-core products, f32 accumulate), f32 core inverse + "
+                    "f64 refinement, f64 control",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R,
-                      "tensor_dtype": "bf16x2 (hi + lo bfloat16 planes, 16 significant bits)",
+                      "tensor_dtype": "f32",
                       "core": "f32 Gauss-Jordan inverse + f64 refinement (<= 8 sweeps, adaptive)",
                       "l2": "flushed between steps",
                       "parallelism": f"replicas x{world}", "global_batch": world},
@@ -468,53 +486,71 @@ def _run_ours(args, rank, world, local):
                                                   "refine_resid", "refine_sweeps")}}
 
     if not args.no_extras and rank == 0:
+        from oracle import cp_oracle as O
+        prob2 = synth.config2(seed, DIMS, dtype="bf16x2")
+        shape2 = cp.make_shape(DIMS, R, "bf16x2")
+        Y2 = cp.tensor_to_device(prob2.Y, "bf16x2")
+        shape64 = cp.make_shape(DIMS, R, "f64")
+        Y64 = cp.tensor_to_device(prob.Y, "f64")          # the float32 values, stored as float64
+
         # --- the tensor pass alone against HBM: this workload and a large one ---
         a_in = cp.factors_to_device(prob.init)
-        mt_ms = time_pass(shape2, Y2, a_in)
+        mt_ms = time_pass(shape32, Y32, a_in)
         bytes_alg = int(np.prod(DIMS)) * 4
         achieved = bytes_alg / (mt_ms * 1e-3) / 1e9
-        out["roofline_tensor_pass"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3 (all-mode MTTKRP + direct residual, one pass)",
-                           "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                           "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_200,
-                           "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": mt_ms,
-                           "algorithmic_bytes": bytes_alg, "peak_kind": "burst (kernel timed alone)"}
+        out["roofline_tensor_pass"] = {"bound": "hbm", "kernel": "k_mttkrp_tc (all-mode MTTKRP + direct residual, "
+                                                                 "one pass, float32 tensor)",
+                                       "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                       "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_TC_200,
+                                       "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": mt_ms,
+                                       "algorithmic_bytes": bytes_alg, "peak_kind": "burst (kernel timed alone)"}
+        mt2_ms = time_pass(shape2, Y2, a_in)
+        out["roofline_tensor_pass_bf16x2"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3 (two-plane tensor)",
+                                              "achieved": bytes_alg / (mt2_ms * 1e-3) / 1e9,
+                                              "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                              "frac": bytes_alg / (mt2_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                              "traffic": TRAFFIC_TC3_200, "ms_per_launch": mt2_ms}
         big = (512, 512, 512)
         gbig = torch.Generator(device="cuda").manual_seed(seed)
-        Ybig = cp.tensor_split(torch.randn(int(np.prod(big)), generator=gbig, device="cuda", dtype=torch.float32))
+        Ybig = torch.randn(int(np.prod(big)), generator=gbig, device="cuda", dtype=torch.float32)
         abig = torch.randn(32 * sum(big), generator=gbig, device="cuda", dtype=torch.float64)
-        sbig = cp.make_shape(big, 32, "bf16x2")
-        big_ms = time_pass(sbig, Ybig, abig)
         bbig = int(np.prod(big)) * 4
-        out["roofline_large"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3", "workload": "512^3, R=32, bf16x2",
+        big_ms = time_pass(cp.make_shape(big, 32, "f32"), Ybig, abig)
+        out["roofline_large"] = {"bound": "hbm", "kernel": "k_mttkrp_tc", "workload": "512^3, R=32, f32",
                                  "achieved": bbig / (big_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": bbig / (big_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                                 "ms_per_launch": big_ms, "algorithmic_bytes": bbig, "traffic": TRAFFIC_512}
+                                 "ms_per_launch": big_ms, "algorithmic_bytes": bbig, "traffic": None}
+        Ybig2 = cp.tensor_split(Ybig)
+        del Ybig
+        big2_ms = time_pass(cp.make_shape(big, 32, "bf16x2"), Ybig2, abig)
+        out["roofline_large_bf16x2"] = {"bound": "hbm", "kernel": "k_mttkrp_tc3", "workload": "512^3, R=32, bf16x2",
+                                        "achieved": bbig / (big2_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                                        "unit": "GB/s", "frac": bbig / (big2_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                        "ms_per_launch": big2_ms, "algorithmic_bytes": bbig,
+                                        "traffic": TRAFFIC_TC3_512}
+        del Ybig2, abig
         # --- the dominant kernel sequence of the step: the float32 core inverse ---
         out["roofline"] = core_inverse_roofline(cp, torch, flush, peaks, peak_src, seed)
-        del Ybig, abig
-        # the float32-tensor form of the same step (tensor-core pass with an
-        # exact float32 residual)
-        prob32 = synth.config2(seed, DIMS, dtype="f32")
-        shape32 = cp.make_shape(DIMS, R, "f32")
-        Y32 = cp.tensor_to_device(prob32.Y, "f32")
-        st32, a32 = new_state(shape32, cp.CP_CORE_MIXED, prob32.init)
-        st32.init(Y32)
-        k32 = max(5, args.steps // 2)
-        t32, _ = timed_steps(st32, a32, Y32, k32, 2)
-        out["f32_tensor_form"] = {"value": k32 / (t32 / 1e3), "unit": "iters/s", "ms_per_step": t32 / k32,
-                                  "mttkrp_ms": time_pass(shape32, Y32, cp.factors_to_device(prob32.init))}
-        st32.close()
+
+        # --- the two-plane tensor form of the same step ---
+        st2, a2 = new_state(shape2, cp.CP_CORE_MIXED, prob2.init)
+        st2.init(Y2)
+        k2 = max(5, args.steps // 2)
+        t2, _ = timed_steps(st2, a2, Y2, k2, 2)
+        out["bf16x2_tensor_form"] = {"value": k2 / (t2 / 1e3), "unit": "iters/s", "ms_per_step": t2 / k2,
+                                     "tensor_dtype": "bf16x2 (hi + lo bfloat16 planes, 16 significant bits)"}
+        st2.close()
 
         # --- ALS sweeps (Sec. 3, Eq. ALS; the initialisation before fLM) on the
-        # same two-plane tensor: N passes over Y per sweep, one per mode ---
-        st_a, a_a = new_state(shape2, cp.CP_CORE_MIXED, prob.init)
-        st_a.init(Y2)
-        st_a.als(Y2, 2)
+        # same tensor: N passes over Y per sweep, one per mode ---
+        st_a, a_a = new_state(shape32, cp.CP_CORE_MIXED, prob.init)
+        st_a.init(Y32)
+        st_a.als(Y32, 2)
         torch.cuda.synchronize()
         ka = 10
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        st_a.als(Y2, ka)
+        st_a.als(Y32, ka)
         e1.record()
         torch.cuda.synchronize()
         als_ms = e0.elapsed_time(e1) / ka
@@ -525,41 +561,37 @@ def _run_ours(args, rank, world, local):
 
         # --- end to end through the public API: float32 tensor on the host ---
         # Every step copies its own input (the pinned float32 tensor) to the
-        # device, splits it into the two-plane form, runs the step (one replay
-        # of a captured one-step graph that reads the split buffer) and reads
-        # its status back.  Two float32 buffers: step k + 1's copy runs on a
-        # copy stream while step k computes; a buffer is overwritten only after
-        # the split that read it has run (the split buffer itself is ordered by
-        # the compute stream).
+        # device, places it in the state's tensor buffer, runs the step (one
+        # replay of a captured one-step graph) and reads its status back.  Two
+        # staging buffers: step k + 1's host copy runs on a copy stream while
+        # step k computes; a staging buffer is overwritten only after the
+        # device copy that read it has run.
         Yh = torch.from_numpy(np.asarray(prob.Y, dtype=np.float32).ravel(order="F")).pin_memory()
-        Yd32 = [torch.empty(Yh.numel(), dtype=torch.float32, device="cuda") for _ in range(2)]
-        Yd2 = torch.empty(2 * Yh.numel(), dtype=torch.bfloat16, device="cuda")
-        st_e, a_e = new_state(shape2, cp.CP_CORE_MIXED, prob.init)
+        Yst = [torch.empty(Yh.numel(), dtype=torch.float32, device="cuda") for _ in range(2)]
+        Yd = torch.empty(Yh.numel(), dtype=torch.float32, device="cuda")
+        st_e, a_e = new_state(shape32, cp.CP_CORE_MIXED, prob.init)
         a_e0 = a_e.clone()
-        Yd32[0].copy_(Yh)
-        cp.tensor_split(Yd32[0], out=Yd2)
-        st_e.init(Yd2)
-        st_e.capture(Yd2, 1)
+        Yd.copy_(Yh)
+        st_e.init(Yd)
+        st_e.capture(Yd, 1)
         for _ in range(args.warmup):
             st_e.launch()
         hst = torch.empty(128, dtype=torch.uint8).pin_memory()
         cur = torch.cuda.current_stream()
         cs = torch.cuda.Stream()
-        ev_c = [torch.cuda.Event(), torch.cuda.Event()]     # copy into buffer b done
-        ev_s = [torch.cuda.Event(), torch.cuda.Event()]     # split of buffer b done
+        ev_c = [torch.cuda.Event(), torch.cuda.Event()]     # host copy into staging buffer b done
+        ev_s = [torch.cuda.Event(), torch.cuda.Event()]     # staging buffer b consumed
         torch.cuda.synchronize()
-        # timed in chunks of at most RESTART_EVERY steps; between chunks (outside
-        # the events) the run restarts from its initial factors
         e2e_ms, done = 0.0, 0
         while done < args.steps:
             a_e.copy_(a_e0)
-            st_e.init(Yd2)
+            st_e.init(Yd)
             chunk = min(RESTART_EVERY, args.steps - done)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             cs.wait_stream(cur)
             with torch.cuda.stream(cs):
-                Yd32[0].copy_(Yh, non_blocking=True)
+                Yst[0].copy_(Yh, non_blocking=True)
                 ev_c[0].record(cs)
             for k in range(chunk):
                 b = k & 1
@@ -567,10 +599,10 @@ def _run_ours(args, rank, world, local):
                     with torch.cuda.stream(cs):
                         if k >= 1:
                             cs.wait_event(ev_s[1 - b])
-                        Yd32[1 - b].copy_(Yh, non_blocking=True)
+                        Yst[1 - b].copy_(Yh, non_blocking=True)
                         ev_c[1 - b].record(cs)
                 cur.wait_event(ev_c[b])
-                cp.tensor_split(Yd32[b], out=Yd2)
+                Yd.copy_(Yst[b])
                 ev_s[b].record(cur)
                 st_e.launch()
                 hst.copy_(st_e.status_tensor(), non_blocking=True)
@@ -580,26 +612,25 @@ def _run_ours(args, rank, world, local):
             done += chunk
         out["e2e"] = {"value": args.steps / (e2e_ms / 1e3), "unit": "iters/s",
                       "h2d_bytes_per_step": Yh.numel() * Yh.element_size(), "d2h_bytes_per_step": 128,
-                      "path": "pinned float32 host tensor -> device (copy stream, two buffers: the next "
-                              "step's copy overlaps this step), cp_tensor_split, one captured cp_dgn_step, status -> host"}
+                      "path": "pinned float32 host tensor -> device staging buffer (copy stream, two buffers: the "
+                              "next step's copy overlaps this step) -> the state's tensor buffer, one captured "
+                              "cp_dgn_step, status -> host"}
         st_e.close()
+        del Yst, Yd
 
         # --- plain float64 form on the float64 tensor ---
-        prob64 = prob                  # the same tensor values, stored as float64
-        shape64 = cp.make_shape(DIMS, R, "f64")
-        Y64 = cp.tensor_to_device(prob64.Y, "f64")
-        st64, a64 = new_state(shape64, cp.CP_CORE_F64, prob64.init)
+        st64, a64 = new_state(shape64, cp.CP_CORE_F64, prob.init)
         st64.init(Y64)
         k64 = max(5, args.steps // 5)
         t64, _ = timed_steps(st64, a64, Y64, k64, 2)
         out["fp64_form"] = {"value": k64 / (t64 / 1e3), "unit": "iters/s", "ms_per_step": t64 / k64,
-                            "tensor_dtype": "f64", "core": "f64 Cholesky", "steps": k64}
+                            "tensor_dtype": "f64 (the float32 values)", "core": "f64 Cholesky", "steps": k64}
         out["speedup_vs_fp64_form"] = value / out["fp64_form"]["value"]
         st64.close()
 
-        # --- time to fit, both forms ---
-        def ttf(shape, Y, prob, mode, cap=3000, chunk=20):
-            s, _ = new_state(shape, mode, prob.init, tol=1e-9, max_iter=cap, mu_max=1e30)
+        # --- time to fit, both forms, and every form against the FP64 oracle ---
+        def ttf(shape, Y, init, mode, cap=3000, chunk=20):
+            s, _ = new_state(shape, mode, init, tol=1e-9, max_iter=cap, mu_max=1e30)
             s.init(Y)
             s.capture(Y, chunk)
             torch.cuda.synchronize()
@@ -612,13 +643,18 @@ def _run_ours(args, rank, world, local):
             t = time.perf_counter() - t0
             s.close()
             return {"seconds": t, "iters": d["iters"], "accepted": d["accepted"], "rel_err": d["rel_err"],
-                    "stop": d["stop_reason"]}
-        ttf2 = ttf(shape2, Y2, prob, cp.CP_CORE_MIXED)
-        ttf64 = ttf(shape64, Y64, prob64, cp.CP_CORE_F64)
-        out["time_to_fit"] = {"mixed": ttf2, "plain_f64": ttf64,
-                              "gain": ttf64["seconds"] / ttf2["seconds"],
-                              "rel_err_diff": abs(ttf2["rel_err"] - ttf64["rel_err"]) / ttf64["rel_err"]}
+                    "stop": d["stop_reason"], "error": d["error"]}
+        ttf32 = ttf(shape32, Y32, prob.init, cp.CP_CORE_MIXED)
+        ttf64 = ttf(shape64, Y64, prob.init, cp.CP_CORE_F64)
+        ttf2 = ttf(shape2, Y2, prob2.init, cp.CP_CORE_MIXED)
+        out["time_to_fit"] = {"mixed": ttf32, "plain_f64": ttf64, "mixed_bf16x2": ttf2,
+                              "gain": ttf64["seconds"] / ttf32["seconds"],
+                              "rel_err_diff": abs(ttf32["rel_err"] - ttf64["rel_err"]) / ttf64["rel_err"]}
+        out["oracle_error"] = oracle_errors(cp, O, torch, prob, prob2, shape32, shape2, shape64, Y32, Y2, Y64,
+                                            {"mixed_f32": ttf32, "plain_f64": ttf64, "mixed_bf16x2": ttf2})
 
+        out["config1"] = bench_config1(cp, O, torch, seed)
+        out["config3"] = bench_config3(cp, O, torch, seed, flush)
         if not args.no_batch:
             out["batched"] = bench_batched(seed)
         if args.serve_seconds > 0:
@@ -629,11 +665,164 @@ def _run_ours(args, rank, world, local):
         out["cpu_baseline"] = {"value": rate, "unit": "iters/s", "cores": oracle_threads(),
                                "kind": "oracle",
                                "sample": f"first {iters} LM iterations of the same 200^3 R=20 problem "
-                                         f"(the same tensor values in float64), {secs:.1f} s",
+                                         f"(the same float32 tensor values in float64), {secs:.1f} s",
                                "one_thread": oracle_rate_one_thread(seed, max(2.0, args.cpu_seconds / 3))}
     st.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def _rel(a, b):
+    import numpy as np
+    a = np.concatenate([np.ravel(np.asarray(x)) for x in a])
+    b = np.concatenate([np.ravel(np.asarray(x)) for x in b])
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_step_delta(cp, torch, shape, Y, A, mu, mode):
+    """One GPU trial from factors A at damping mu (no normalisation): its step."""
+    a = cp.factors_to_device(A)
+    st = cp.State(shape, a, mu0=float(mu), max_iter=10, core_mode=mode, normalize=False, refine_iters=8)
+    st.init(Y)
+    st.step(Y)
+    torch.cuda.synchronize()
+    dims = [x.shape[0] for x in A]
+    Rr = A[0].shape[1]
+    d = [x.numpy().copy() for x in cp.split_factors(st.buffer(cp.State.BUF_DELTA, Rr * sum(dims)).cpu(), dims, Rr)]
+    s = st.status()
+    st.close()
+    return d, s
+
+
+def core_kappa(O, A, mu):
+    import numpy as np
+    ev = np.linalg.eigvalsh(O.spd_core(A, mu))
+    return float(ev[-1] / ev[0])
+
+
+def oracle_errors(cp, O, torch, prob, prob2, shape32, shape2, shape64, Y32, Y2, Y64, ttfs):
+    """Every form against the FP64 oracle: (1) one step from a fixed state of
+    the oracle's own trajectory (after 20 LM iterations from the seeded start,
+    where mu is already well below its start), relative to the oracle's
+    fLM_a step, with kappa of the core there; (2) the final epsilon of the
+    form's run to its stop rule (relative fit change < 1e-9) against the
+    oracle's run to the same rule on the same tensor values."""
+    out = {}
+    t0 = time.perf_counter()
+    ref32 = O.lm_fit(prob.Y, prob.init, mu0=None, max_iter=3000, tol=1e-9)
+    ref2 = O.lm_fit(prob2.Y, prob2.init, mu0=None, max_iter=3000, tol=1e-9)
+    mid32 = O.lm_fit(prob.Y, prob.init, mu0=None, max_iter=20, tol=0.0)
+    mid2 = O.lm_fit(prob2.Y, prob2.init, mu0=None, max_iter=20, tol=0.0)
+    for name, pr, ref, mid, shape, Y, mode in (
+            ("plain_f64", prob, ref32, mid32, shape64, Y64, cp.CP_CORE_F64),
+            ("mixed_f32", prob, ref32, mid32, shape32, Y32, cp.CP_CORE_MIXED),
+            ("mixed_bf16x2", prob2, ref2, mid2, shape2, Y2, cp.CP_CORE_MIXED)):
+        d, s = gpu_step_delta(cp, torch, shape, Y, mid.A, mid.mu, mode)
+        ost = O.flm_step(pr.Y, mid.A, mid.mu)
+        ttf = ttfs[name]
+        out[name] = {"step_rel_err": _rel(d, ost.delta), "step_state": {"oracle_iter": 20, "mu": mid.mu,
+                                                                        "kappa_core": core_kappa(O, mid.A, mid.mu)},
+                     "refine_sweeps": s["refine_sweeps"], "refine_resid": s["refine_resid"],
+                     "final_eps": ttf["rel_err"], "oracle_final_eps": ref.rel_err,
+                     "final_eps_rel_err": abs(ttf["rel_err"] - ref.rel_err) / ref.rel_err,
+                     "iters": ttf["iters"], "oracle_iters": ref.iters, "oracle_stop": ref.stop}
+    out["oracle_seconds"] = time.perf_counter() - t0
+    return out
+
+
+def bench_config1(cp, O, torch, seed):
+    """20^3, R = 5, float64, mu_0 = 1, 200 LM iterations (graph-captured in
+    one launch): microseconds per step and the 200-iteration wall time, and
+    the final epsilon against the oracle's 200 iterations from the same start."""
+    from paper_1205_2584_gb300 import synth
+    p = synth.config1(seed)
+    shape = cp.make_shape(p.dims, p.R, "f64")
+    Y = cp.tensor_to_device(p.Y, "f64")
+    a = cp.factors_to_device(p.init)
+    a0 = a.clone()
+    st = cp.State(shape, a, mu0=1.0, max_iter=200, mu_max=float("inf"), core_mode=cp.CP_CORE_F64)
+    st.capture(Y, 200)
+    times = []
+    for _ in range(4):
+        a.copy_(a0)
+        st.init(Y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    s = st.status()
+    st.close()
+    ref = O.lm_fit(p.Y, p.init, mu0=1.0, max_iter=200, tol=0.0, mu_max=float("inf"))
+    ms = statistics.median(times[1:])
+    return {"workload": "cp3-20^3-R5-f64-snr30, mu0 = 1, 200 iterations", "us_per_step": 1e3 * ms / 200,
+            "wall_ms_200_iters": ms, "iters": s["iters"], "rel_err": s["rel_err"],
+            "oracle_rel_err": ref.rel_err, "final_eps_rel_err": abs(s["rel_err"] - ref.rel_err) / ref.rel_err,
+            "core": "f64 Cholesky"}
+
+
+def bench_config3(cp, O, torch, seed, flush):
+    """60^4, R = 15 (core N R^2 = 900), column norms log-uniform over
+    [1e-2, 1e2], SNR 30 dB, bfloat16 tensor: iterations/s of the mixed form
+    and the float64 form (float64 tensor of the same values), their
+    time-to-fit (relative fit change < 1e-9, at most 1500 trials), and one
+    step of each against the oracle's step from the seeded start."""
+    from paper_1205_2584_gb300 import synth
+    p = synth.config3(seed)
+    out = {"workload": "cp4-60^4-R15-lognorm(1e-2..1e2)-snr30, bf16 tensor"}
+    forms = (("mixed_bf16", cp.make_shape(p.dims, p.R, "bf16"), cp.tensor_to_device(p.Y, "bf16"),
+              cp.CP_CORE_MIXED),
+             ("plain_f64", cp.make_shape(p.dims, p.R, "f64"), cp.tensor_to_device(p.Y, "f64"), cp.CP_CORE_F64))
+    mu0 = O.initial_mu(p.init, 1e-3)
+    ost = O.flm_step(p.Y, p.init, mu0)
+    for name, shape, Y, mode in forms:
+        a = cp.factors_to_device(p.init)
+        a0 = a.clone()
+        st = cp.State(shape, a, mu0=-1.0, tau=1e-3, max_iter=10 ** 9, mu_max=float("inf"), core_mode=mode,
+                      refine_iters=8)
+        st.init(Y)
+        st.capture(Y, 1)
+        for _ in range(3):
+            st.launch()
+        K = 20
+        ev = []
+        for i in range(K):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.launch()
+            e1.record()
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(x.elapsed_time(y) for x, y in ev) / K
+        st.close()
+        # time to fit
+        a.copy_(a0)
+        st = cp.State(shape, a, mu0=-1.0, tau=1e-3, tol=1e-9, max_iter=1500, mu_max=1e30, core_mode=mode,
+                      refine_iters=8)
+        st.init(Y)
+        st.capture(Y, 20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while True:
+            st.launch()
+            d = st.status()
+            if d["stop"] != 0:
+                break
+        tf = time.perf_counter() - t0
+        st.close()
+        dl, _ = gpu_step_delta(cp, torch, shape, Y, p.init, mu0, mode)
+        out[name] = {"iters_per_s": 1e3 / ms, "ms_per_step": ms, "time_to_fit_s": tf, "iters": d["iters"],
+                     "accepted": d["accepted"], "rel_err": d["rel_err"], "stop": d["stop_reason"],
+                     "step_rel_err_vs_oracle": _rel(dl, ost.delta)}
+    out["iters_per_s_gain"] = out["mixed_bf16"]["iters_per_s"] / out["plain_f64"]["iters_per_s"]
+    out["time_to_fit_gain"] = out["plain_f64"]["time_to_fit_s"] / out["mixed_bf16"]["time_to_fit_s"]
+    out["final_eps_mixed_vs_f64"] = abs(out["mixed_bf16"]["rel_err"] - out["plain_f64"]["rel_err"]) / \
+        out["plain_f64"]["rel_err"]
+    out["step_state"] = {"mu": mu0, "kappa_core": core_kappa(O, p.init, mu0)}
+    return out
 
 
 def _ttf_state(cp, shape, Y, a0, mode, tol, cap=1000, chunk=20):
@@ -700,7 +889,15 @@ def bench_batched(seed):
         t64 += dt
         it64 += d["iters"]
     per64 = t64 / len(sample)
-    return {"workload": "512 problems, I_n~U{10..64}, R~U{3..12}, mode-1 collinearity 0.8, snr30, f32",
+    # final epsilon of sampled problems against the oracle's run to the same
+    # stop rule on the same float32 values
+    from oracle import cp_oracle as O
+    errs = []
+    for k in sample[:4]:
+        ref = O.lm_fit(probs[k].Y, probs[k].init, mu0=None, max_iter=1000, tol=1e-8)
+        errs.append(abs(st[k]["rel_err"] - ref.rel_err) / ref.rel_err)
+    return {"oracle_final_eps_rel_err": {"max": max(errs), "sample": [int(k) for k in sample[:4]]},
+            "workload": "512 problems, I_n~U{10..64}, R~U{3..12}, mode-1 collinearity 0.8, snr30, f32",
             "value": iters / t, "unit": "iters/s", "seconds_all_512": t, "problems_per_s": 512 / t,
             "trials_total": iters, "stops": stops, "tile": cfg["tile"], "order": cfg["order"],
             "graph": "one captured persistent launch",
@@ -741,12 +938,21 @@ def bench_served(seed, seconds, rate, slots=4):
         r = srv.serve([req], realtime=False)[0]
         t32 = time.perf_counter() - t32
         y64, a64 = S.synth_on_device(req, srv.device, torch.float64)
-        if S.two_plane_ok(d, R):          # the served request ran on the hi + lo values
+        if r.path == "lane":              # lanes run on the float32 values
+            y64 = y64.float().double()
+        elif S.two_plane_ok(d, R):        # a State request ran on the hi + lo values
             y2 = cp.tensor_split(y64.float())
             y64 = y2[:y64.numel()].double() + y2[y64.numel():].double()
         dt, d64 = _ttf_state(cp, cp.make_shape(d, R, "f64"), y64, a64, cp.CP_CORE_F64, tol=1e-8)
-        alone["x".join(map(str, d)) + f"-R{R}"] = {"mixed_s": t32, "mixed_iters": r.status["iters"],
-                                                  "f64_s": dt, "f64_iters": d64["iters"], "gain": dt / t32}
+        entry = {"mixed_s": t32, "mixed_iters": r.status["iters"], "f64_s": dt, "f64_iters": d64["iters"],
+                 "gain": dt / t32}
+        if d[0] <= 128:            # the oracle's run to the same stop rule on the same values
+            from oracle import cp_oracle as O
+            Yh = y64.cpu().numpy().reshape(d, order="F")
+            A0 = [x.numpy().copy() for x in cp.split_factors(a64.cpu(), d, R)]
+            ref = O.lm_fit(Yh, A0, mu0=None, max_iter=1000, tol=1e-8)
+            entry["oracle_final_eps_rel_err"] = abs(r.status["rel_err"] - ref.rel_err) / ref.rel_err
+        alone["x".join(map(str, d)) + f"-R{R}"] = entry
         del y64, a64
     out["alone_vs_fp64_form"] = alone
     srv.close()

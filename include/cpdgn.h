@@ -62,8 +62,11 @@ enum cp_code {
   CP_OK = 0,
   CP_EINVAL = 1,      /* bad argument: null pointer, N, R or I out of range */
   CP_ENOTSPD = 2,     /* core system or Gamma^(n) + mu I not positive definite */
-  CP_ENONFINITE = 3,  /* NaN or Inf met on the device */
-  CP_ETIMEOUT = 4,    /* reserved for bounded device waits */
+  CP_ENONFINITE = 3,  /* NaN or Inf met on the device: in the tensor or the
+                         initial factors (cp_state_init stops the run), or in
+                         a trial's step or residual (the trial is rejected) */
+  CP_ETIMEOUT = 4,    /* a bounded device wait ran out (tensor-core pass);
+                         the run stops with CP_STOP_ERROR */
   CP_ENOMEM = 5,      /* workspace smaller than cp_workspace_bytes() */
   CP_ECUDA = 6        /* a CUDA runtime call failed */
 };
@@ -119,7 +122,11 @@ typedef struct cp_status {
   int32_t iters;           /* trial steps taken */
   int32_t accepted;        /* accepted steps */
   int32_t stop;            /* enum cp_stop */
-  int32_t error;           /* enum cp_code of the first device-side error */
+  int32_t error;           /* enum cp_code of the first device-side error:
+                              CP_ENONFINITE (see cp_code), CP_ETIMEOUT, CP_EINVAL
+                              (all-zero tensor: epsilon undefined), CP_ENOTSPD
+                              (cp_als_sweep only; a failed core factorisation
+                              in a trial only sets `info` and rejects it) */
   int32_t last_accepted;   /* 1 if the last trial was accepted */
   int32_t info;            /* first non-positive pivot (1-based) of the last factorisation */
   int32_t refine_sweeps;   /* refinement residuals formed by the last CP_CORE_MIXED solve */
@@ -153,10 +160,12 @@ int cp_gram(const cp_shape* shape, const double* a, double* C, double* Gamma_nm,
  * this call.  Its scratch (the per-row-block partial sums) is a fixed
  * 2 MiB float64 array inside the library, present on every GPU that loads the
  * library until the process exits; shapes whose partial sums exceed it
- * (more than 2^18 doubles: ceil(I_n/8) summed over n, times R(R+1)/2 + R^2)
+ * (more than 2^18 doubles: ceil(I_n/8) summed over n, times R(R+1)/2)
  * return CP_ENOMEM.  The call allocates nothing.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress, with that device
- * current) and caches it, so make that first call before any stream capture.
+ * current) and caches it per device ordinal, so make that first call before
+ * any stream capture; after cudaDeviceReset the cached address is no longer
+ * valid, so do not call this again on a device the process has reset.
  * All calls share the array: calls that overlap on the GPU race; order them
  * (one stream, or events). */
 int cp_gram_noalloc(const cp_shape* shape, const double* a, double* C, double* Gamma_nm,
@@ -250,7 +259,11 @@ int cp_state_destroy(cp_state* st);
 
 /* Start a decomposition of Y from the current contents of `a`: one pass over
  * Y for the MTTKRP, ||Y - Y_hat||^2 and ||Y||^2; sets mu_0 (Eq. mu0 or
- * opts->mu0), nu = 2 and the counters. */
+ * opts->mu0), nu = 2 and the counters.  If ||Y||^2, the residual or mu_0 is
+ * not finite (NaN / Inf in Y or in `a`) the status gets error = CP_ENONFINITE
+ * and stop = CP_STOP_ERROR (an all-zero Y: CP_EINVAL); later steps are then
+ * no-ops.  It also records the device's count of timed-out tensor-core waits,
+ * so that cp_dgn_step can report one that happens later. */
 int cp_state_init(cp_state* st, const void* Y, void* stream);
 
 /* One damped Gauss-Newton trial: Gramians, damped inverses, w, core build and
@@ -260,8 +273,24 @@ int cp_state_init(cp_state* st, const void* Y, void* stream);
  * normalisation and the stop test -- all on the device, with no host
  * synchronisation, so a sequence of calls can be captured in a CUDA graph.
  * Once the device status says stop != CP_RUNNING every later call is a no-op
- * on the device. */
+ * on the device.  Failure handling (Sec. 4.6 leaves it open): a trial whose
+ * core system or Gamma^(n) + mu I is not positive definite (status.info =
+ * the first bad pivot, 1-based), or whose step or residual is not finite
+ * (status.error = CP_ENONFINITE unless an error is recorded already), is
+ * rejected with rho = 0, so mu grows by nu; a bounded device wait of the
+ * tensor-core pass that ran out since cp_state_init (counted per device, over
+ * every call of the process) stops the run with error = CP_ETIMEOUT. */
 int cp_dgn_step(cp_state* st, const void* Y, void* stream);
+
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * CTA initialises an mbarrier that nothing ever arrives at and waits on it
+ * with the same bounded wait the tensor-core pass uses, limited to limit_ns
+ * nanoseconds (1e3 .. 1e10); no copy or tensor-core operation is in flight.
+ * The wait runs out, the kernel returns normally and adds one to the
+ * device's count of timed-out waits, which a state initialised before this
+ * call reports at its next cp_dgn_step as CP_ETIMEOUT.  CP_EINVAL for a
+ * limit out of range. */
+int cp_selftest_wait_timeout(int64_t limit_ns, void* stream);
 
 /* Capture `steps` consecutive cp_dgn_step calls on `stream` into a CUDA graph
  * owned by the state (replacing any earlier one).  Nothing runs during the

@@ -22,7 +22,10 @@ _CACHE: Dict[str, dict] = {}
 
 
 def signature(batch) -> str:
-    shapes = sorted((tuple(d), R) for d, R, _ in batch.meta)
+    """Key of the cache: the problem shapes in queue order.  The order is kept
+    (not sorted) because the "given" queue order is one of the tuned choices,
+    and its speed depends on where the expensive problems sit."""
+    shapes = [(tuple(d), R) for d, R, _ in batch.meta]
     return hashlib.sha1(json.dumps(shapes).encode()).hexdigest()[:16]
 
 

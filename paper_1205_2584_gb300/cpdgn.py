@@ -85,6 +85,7 @@ _sig = {
     "cp_batch_run": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                      ctypes.c_int, _vp, _vp],
     "cp_tensor_split": [_vp, ctypes.c_int64, _vp, _vp],
+    "cp_selftest_wait_timeout": [ctypes.c_int64, _vp],
     "cp_spd_invert_f32": [ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int),
                           _vp],
 }
@@ -449,3 +450,8 @@ class Batch:
     def factors(self, i: int):
         dims, R, aoff = self.meta[i]
         return split_factors(self.a[aoff:aoff + R * sum(dims)].cpu(), dims, R)
+
+
+def selftest_wait_timeout(limit_ns: int = 1_000_000, stream=None):
+    """cp_selftest_wait_timeout: one bounded device wait that runs out (see the header)."""
+    _check(_lib.cp_selftest_wait_timeout(int(limit_ns), _stream(stream)), "cp_selftest_wait_timeout")

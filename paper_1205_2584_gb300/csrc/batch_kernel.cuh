@@ -975,6 +975,11 @@ __global__ void __launch_bounds__(BT) k_batch_lm(const cp_batch_problem* probs, 
         st->accepted = 0;
         st->last_accepted = 0;
         st->info = 0;
+        // NaN / Inf in the tensor or the factors, or an all-zero tensor: stop
+        if (!isfinite(yn) || !isfinite(r2) || !isfinite(st->mu) || !(yn > 0.0)) {
+          st->error = (isfinite(yn) && isfinite(r2) && isfinite(st->mu)) ? CP_EINVAL : CP_ENONFINITE;
+          st->stop = CP_STOP_ERROR;
+        }
       }
       __syncthreads();
     }
@@ -993,8 +998,12 @@ __global__ void __launch_bounds__(BT) k_batch_lm(const cp_batch_problem* probs, 
       // control
       if (threadIdx.x == 0) {
         const double r2 = st->resid2;
-        const bool accept = ok && isfinite(r2t) && (r2t < r2);
-        const double rho = (den > 0.0 && isfinite(r2t)) ? (r2 - r2t) / den : 0.0;
+        const bool finite = isfinite(r2t) && isfinite(den);
+        const bool accept = ok && finite && (r2t < r2);
+        // a failed factorisation or a non-finite trial is rejected as rho = 0
+        // (mu grows), as in the single-problem control
+        const double rho = (ok && finite && den > 0.0) ? (r2 - r2t) / den : 0.0;
+        if (ok && !finite && st->error == 0) st->error = CP_ENONFINITE;
         double m2 = st->mu, nu = st->nu;
         if (rho > 0.0) {
           const double tt = 2.0 * rho - 1.0;

@@ -176,7 +176,10 @@ constexpr int kMaxDevices = 64;
 static double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of g_gram_scratch on the current device, looked up once per
-// device (cudaGetSymbolAddress with that device current) and cached.
+// device (cudaGetSymbolAddress with that device current) and cached.  The
+// cache is keyed by device ordinal: after cudaDeviceReset (which unloads the
+// module) the cached address is stale, so a process that resets a device
+// must not call cp_gram_noalloc on it again.
 static int noalloc_scratch(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CP_ECUDA;
@@ -198,7 +201,8 @@ extern "C" int cp_gram_noalloc(const cp_shape* shape, const double* a, double* C
   Dims d;
   CP_TRY(make_dims(shape, &d));
   if (!a || !C) return CP_EINVAL;
-  if (gram_part_bytes(d) > kNoallocScratchDoubles * sizeof(double)) return CP_ENOMEM;
+  // this call never forms P = A^T M, so its partials need R(R+1)/2 doubles per chunk
+  if (size_t(gram_chunks(d)) * gram_entries(d.R, false) > kNoallocScratchDoubles) return CP_ENOMEM;
   double* scratch = nullptr;
   CP_TRY(noalloc_scratch(&scratch));
   return launch_gram(d, a, nullptr, scratch, C, nullptr, Gamma_nm, Gamma_all, nullptr,

@@ -936,6 +936,24 @@ static int launch_tc3(const Dims& d, const void* Y, const double* a, double* m, 
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
+// Device address of g_tc_timeouts on the current device (looked up once per
+// device; the counter counts the bounded waits of the tensor-core passes
+// that ran out, over every call of the process on that device).
+int tc_timeout_counter(int** out) {
+  static std::mutex mu;
+  static int* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CP_ECUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tc_timeouts) != cudaSuccess) return CP_ECUDA;
+    addr[dev] = static_cast<int*>(p);
+  }
+  *out = addr[dev];
+  return CP_OK;
+}
+
 // CP_EINVAL when the shape or pointers do not suit a tensor-core pass (the
 // caller falls back to the SIMT kernels); m and resid2 must be zeroed.
 int launch_mttkrp_tc(const Dims& d, const void* Y, const double* a, double* m, double* resid2, const int* skip,
@@ -977,6 +995,29 @@ int launch_mttkrp_tc(const Dims& d, const void* Y, const double* a, double* m, d
 }
 
 }  // namespace cpdgn
+
+namespace cpdgn {
+// An mbarrier that expects one arrival which never comes: the bounded wait
+// gives up after limit_ns and the event is counted like a timed-out wait of
+// the pass.  Nothing asynchronous is issued, so there is nothing to drain.
+__global__ void k_selftest_wait(uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) ok = tc::mbar_wait(&bar, 0, limit_ns);
+  if (threadIdx.x == 0 && !ok) atomicAdd(&g_tc_timeouts, 1);
+}
+}  // namespace cpdgn
+
+extern "C" int cp_selftest_wait_timeout(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 10000000000ll) return CP_EINVAL;
+  cpdgn::k_selftest_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(uint64_t(limit_ns));
+  return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
+}
 
 extern "C" int cp_tensor_split(const float* Y, int64_t J, void* out, void* stream) {
   if (!Y || !out || J < 1 || (reinterpret_cast<uintptr_t>(out) & 15) != 0) return CP_EINVAL;

@@ -53,6 +53,7 @@ int chol_solve(const T* L, int64_t n, TX* x, TX* tmp, TX* y, const int* skip, cu
 template <typename T>
 int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const int* skip, cudaStream_t s,
               cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result);
+int tc_timeout_counter(int** out);
 int launch_gemv_acc(const float* X, int64_t n, const double* r, double* y, const double* b2, const double* r2,
                     const double* r2prev, int* done, double tol2, const int* skip, cudaStream_t s);
 
@@ -60,7 +61,7 @@ int launch_gemv_acc(const float* X, int64_t n, const double* r, double* y, const
 enum { SC_R2T = 0, SC_YN2 = 1, SC_R2 = 2, SC_REFN = 3, SC_NRM = 8 };   // SC_NRM..: ||b||^2, ||res_k||^2
 constexpr int kMaxRefine = 48;
 // int slots inside S_INFO
-enum { IN_INFO = 0, IN_COMMIT = 1, IN_ZERO = 2, IN_RDONE = 3 };
+enum { IN_INFO = 0, IN_COMMIT = 1, IN_ZERO = 2, IN_RDONE = 3, IN_TOBASE = 4 };
 
 struct Bufs {
   double *C, *Gnm, *Gall, *P, *LC, *U, *Gt, *w, *Kw, *b, *y, *Z, *res, *dcor, *f, *Wp;
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kUpdRows * 32) k_update(Dims d, const double* 
 }
 
 __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_status* st,
-                          double* scal, int* info, double* scale) {
+                          double* scal, int* info, double* scale, const int* tmo) {
   // One CTA of 256 threads.  The float64 square roots, divides and roots
   // below are long dependent operations on this part (hundreds of cycles
   // each), so independent ones run on different threads: the two relative
@@ -252,8 +253,17 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
     const double r2 = st->resid2;
     const double r2t = scal[SC_R2T];
     const int bad = info[IN_INFO];
-    const bool accept = (bad == 0) && isfinite(r2t) && (r2t < r2);
-    const double rho = (den > 0.0 && isfinite(r2t)) ? (r2 - r2t) / den : 0.0;
+    const bool finite = isfinite(r2t) && isfinite(den);
+    const bool accept = (bad == 0) && finite && (r2t < r2);
+    // a trial whose core factorisation failed, or whose step or residual is
+    // not finite, is rejected and counts as rho = 0, so mu always grows then
+    const double rho = (bad == 0 && finite && den > 0.0) ? (r2 - r2t) / den : 0.0;
+    // (a failed factorisation leaves undefined values behind it; only a trial
+    // whose factorisations succeeded reports non-finite numbers as an error)
+    if (bad == 0 && !finite && st->error == 0) st->error = CP_ENONFINITE;
+    // a bounded device wait of the tensor-core pass ran out since cp_state_init
+    // (its outputs were poisoned, so this trial is rejected): stop with an error
+    const bool timed_out = tmo && (*reinterpret_cast<const volatile int*>(tmo) != info[IN_TOBASE]);
     double mu = st->mu, nu = st->nu;
     if (rho > 0.0) {
       const double t = 2.0 * rho - 1.0;
@@ -280,6 +290,10 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
       st->resid2 = r2t;
       st->rel_err = e_new;
       if (e_old > 0.0 && fabs(e_old - e_new) < o.tol * e_old) st->stop = CP_STOP_TOL;
+    }
+    if (timed_out) {
+      st->error = CP_ETIMEOUT;
+      st->stop = CP_STOP_ERROR;
     }
     if (st->stop == CP_RUNNING && mu > o.mu_max) st->stop = CP_STOP_MU;
     if (st->stop == CP_RUNNING && st->iters >= o.max_iter) st->stop = CP_STOP_MAXIT;
@@ -339,7 +353,7 @@ __global__ void k_sumsq(const void* Y, int dtype, int64_t J, double* out) {
 }
 
 __global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double* scal, cp_status* st,
-                              double* mu_copy) {
+                              double* mu_copy, const int* tmo, int* info) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double mx = 0.0;
   for (int n = 0; n < d.N; ++n)
@@ -366,8 +380,17 @@ __global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double
   s.info = 0;
   s.refine_sweeps = 0;
   s.reserved_i[0] = 0;
+  // a tensor or factors with NaN / Inf entries give a non-finite ||Y||^2 or
+  // residual: nothing can be decided from them, so the run stops at once
+  if (!isfinite(s.y_norm2) || !isfinite(s.resid2) || !isfinite(s.mu) || !(s.y_norm2 > 0.0)) {
+    s.error = isfinite(s.y_norm2) && isfinite(s.resid2) && isfinite(s.mu) ? CP_EINVAL : CP_ENONFINITE;
+    s.stop = CP_STOP_ERROR;
+  }
   *st = s;
   *mu_copy = s.mu;
+  // the timeout counter of the tensor-core pass as it stands now; k_control
+  // reports CP_ETIMEOUT once it moves
+  info[IN_TOBASE] = tmo ? *reinterpret_cast<const volatile int*>(tmo) : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -426,6 +449,7 @@ struct cp_state {
   cudaStream_t rhs = nullptr;            // third stream: the core system's right-hand side
   cudaEvent_t ev_rhs_fork = nullptr, ev_rhs_join = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int* tmo = nullptr;                    // device counter of timed-out waits of the tensor-core pass
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_steps = 0;
@@ -512,6 +536,10 @@ extern "C" int cp_state_create(const cp_shape* shape, const cp_opts* opts, doubl
   st->ws = ws;
   st->L = L;
   st->B = carve(L, ws, d.ncore);
+  if (tc_timeout_counter(&st->tmo) != CP_OK) {
+    delete st;
+    return CP_ECUDA;
+  }
   if (opts->core_mode == CP_CORE_MIXED) {
     if (cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&st->rhs, cudaStreamNonBlocking) != cudaSuccess ||
@@ -652,7 +680,7 @@ extern "C" int cp_state_init(cp_state* st, const void* Y, void* stream) {
   if (g > 4 * kSMs) g = 4 * kSMs;
   k_sumsq<<<unsigned(g), 256, 0, s>>>(Y, d.y_dtype, d.J, B.scal + SC_YN2);
   CP_TRY(launch_gram(d, st->a, nullptr, B.gpart, B.C, nullptr, B.Gnm, B.Gall, nullptr, s));
-  k_init_status<<<1, 32, 0, s>>>(d, st->o, B.Gnm, B.scal, B.status, B.mu);
+  k_init_status<<<1, 32, 0, s>>>(d, st->o, B.Gnm, B.scal, B.status, B.mu, st->tmo, B.info);
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -692,7 +720,7 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
   k_update<<<unsigned(nupd), kUpdRows * 32, 0, s>>>(d, st->a, B.m, B.Gnm, B.Gt, B.f, mu, B.delta, B.at,
                                                     B.part, skip);
   CP_TRY(launch_mttkrp(d, Y, B.at, B.mt, B.scal + SC_R2T, skip, s));
-  k_control<<<1, 256, 0, s>>>(d, st->o, B.part, nupd, B.status, B.scal, B.info, B.scale);
+  k_control<<<1, 256, 0, s>>>(d, st->o, B.part, nupd, B.status, B.scal, B.info, B.scale, st->tmo);
   int64_t gc = (nm + 255) / 256;
   if (gc > 4 * kSMs) gc = 4 * kSMs;
   k_commit<<<unsigned(gc), 256, 0, s>>>(d, B.info + IN_COMMIT, B.at, B.mt, B.scale, st->a, B.m);

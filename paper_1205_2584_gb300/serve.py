@@ -143,19 +143,32 @@ def poisson_requests(seed: int = 0, rate: float = 200.0, seconds: float = 60.0) 
 
 
 def summarize(results: List[Result], wall: float) -> dict:
-    """p50 / p99 / mean time-to-fit (overall and per shape class), throughput."""
+    """p50 / p99 / mean time-to-fit (overall and per shape class), throughput.
+    Per class the time-to-fit is also split into its queue part (arrival to
+    admission: waiting for a slot, arena space or HBM budget) and its run
+    part (admission to the stop flag being seen on the host)."""
     ttf = np.array([r.time_to_fit for r in results]) if results else np.zeros(1)
     trials = sum(r.status["iters"] for r in results)
-    by: Dict[str, List[float]] = {}
+    by: Dict[str, List[Result]] = {}
     for r in results:
         key = "x".join(map(str, r.status["dims"])) + f"-R{r.status['R']}"
-        by.setdefault(key, []).append(r.time_to_fit)
+        by.setdefault(key, []).append(r)
+
+    def cls(v: List[Result]) -> dict:
+        t = np.array([r.time_to_fit for r in v])
+        q = np.array([r.admitted - r.arrival for r in v])
+        u = np.array([r.done - r.admitted for r in v])
+        it = np.array([r.status["iters"] for r in v], dtype=float)
+        return {"n": len(v), "p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
+                "queue_p50_s": float(np.percentile(q, 50)), "queue_p99_s": float(np.percentile(q, 99)),
+                "run_p50_s": float(np.percentile(u, 50)), "run_p99_s": float(np.percentile(u, 99)),
+                "iters_p50": float(np.percentile(it, 50)), "iters_p99": float(np.percentile(it, 99))}
+
     return {"requests": len(results), "p50_s": float(np.percentile(ttf, 50)),
             "p99_s": float(np.percentile(ttf, 99)), "mean_s": float(ttf.mean()),
             "throughput_req_s": len(results) / wall if wall > 0 else 0.0,
             "trials_per_s": trials / wall if wall > 0 else 0.0,
-            "by_class": {k: {"n": len(v), "p50_s": float(np.percentile(v, 50)),
-                             "p99_s": float(np.percentile(v, 99))} for k, v in sorted(by.items())}}
+            "by_class": {k: cls(v) for k, v in sorted(by.items())}}
 
 
 # ---------------------------------------------------------------------------

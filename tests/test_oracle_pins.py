@@ -356,6 +356,95 @@ def test_accepted_errors_monotone():
     assert np.all(np.diff(h) <= 1e-15)
 
 
+
+def test_initial_mu_is_tau_times_max_diag_of_JtJ():
+    """Eq. mu0: mu_0 = tau max diag(H), H = J^T J formed from the explicit
+    Jacobian (Lemma 2).  The column norms differ per mode and component so
+    that max diag Gamma^(n), max diag C^(n) and max diag of the all-mode
+    Hadamard product Gamma are three different numbers; only the first is
+    right."""
+    rng = np.random.default_rng(40)
+    dims, R = (3, 4, 5), 3
+    scales = [np.array([1.0, 3.0, 0.5]), np.array([2.0, 0.2, 1.5]), np.array([0.7, 4.0, 1.1])]
+    A = [rng.standard_normal((I, R)) * s[None, :] for I, s in zip(dims, scales)]
+    J = O.jacobian(A)
+    hmax = float(np.max(np.diag(J.T @ J)))
+    for tau in (1e-3, 0.5):
+        assert O.initial_mu(A, tau) == pytest.approx(tau * hmax, rel=1e-13)
+    g = O.grams(A)
+    wrong = {float(np.max([np.max(np.diag(c)) for c in g.C])), float(np.max(np.diag(g.Gamma_all)))}
+    for w in wrong:
+        assert abs(w - hmax) > 1e-3 * hmax
+
+
+def test_initial_mu_hand_computed_example():
+    """Two 2 x 2 factors with orthogonal columns: diag Gamma^(1) = diag C^(2),
+    diag Gamma^(2) = diag C^(1); with column norms^2 (1, 4) and (9, 0.25) the
+    largest diagonal entry of H is 9 (printed rule: tau times it)."""
+    A = [np.array([[1.0, 0.0], [0.0, 2.0]]), np.array([[3.0, 0.0], [0.0, 0.5]])]
+    assert O.initial_mu(A, 1.0) == pytest.approx(9.0, rel=1e-15)
+    assert O.initial_mu(A, 1e-3) == pytest.approx(9e-3, rel=1e-15)
+
+
+def test_initial_mu_unit_columns_special_case():
+    """Eq. mu0's last form: with unit-length columns in modes n < N,
+    max diag H = max{1, diag C^(N)}."""
+    rng = np.random.default_rng(41)
+    dims, R = (4, 5, 6), 3
+    A = [rng.standard_normal((I, R)) for I in dims]
+    for n in range(2):
+        A[n] /= np.linalg.norm(A[n], axis=0)
+    for s in (0.3, 2.5):                      # last-mode norms below / above 1
+        B = [A[0], A[1], A[2] / np.linalg.norm(A[2], axis=0) * s]
+        expect = max(1.0, float(np.max(np.diag(B[2].T @ B[2]))))
+        assert O.initial_mu(B, 1.0) == pytest.approx(expect, rel=1e-13)
+
+
+def test_lm_fit_relative_change_stop_on_constructed_history():
+    """Sec. 4.6 stop rule as read here: stop on the first ACCEPTED trial whose
+    relative change of epsilon is below tol.  A reference run (tol = 0) gives
+    the history; tol is then placed between that trial's change and every
+    earlier accepted change, and the run must stop exactly there, with the
+    factors of the reference run at that trial."""
+    p = synth.make_problem(42, (7, 8, 9), 3, snr_db=30, collinearity=(0.8, 0.8, 0.8))
+    eps0 = O.rel_error(p.Y, p.init)
+    ref = O.lm_fit(p.Y, p.init, mu0=1.0, max_iter=30, tol=0.0)
+    h = [eps0] + list(ref.history)
+    acc = [h[t + 1] != h[t] for t in range(len(ref.history))]
+    chg = [abs(h[t] - h[t + 1]) / h[t] for t in range(len(ref.history))]
+    assert any(not a for a in acc[:25]), "the constructed history should hold a rejected trial"
+    run_min, target = math.inf, None
+    for t in range(len(chg)):
+        if not acc[t]:
+            continue
+        if t >= 4 and chg[t] < run_min:
+            target = t
+            break
+        run_min = min(run_min, chg[t])
+    assert target is not None
+    tol = 0.5 * (chg[target] + run_min)
+    res = O.lm_fit(p.Y, p.init, mu0=1.0, max_iter=30, tol=tol)
+    assert res.stop == "tol"
+    assert res.iters == target + 1
+    assert res.history == ref.history[:target + 1]
+    ref_t = O.lm_fit(p.Y, p.init, mu0=1.0, max_iter=target + 1, tol=0.0)
+    assert _rel(res.A, ref_t.A) == 0.0
+    # a rejected trial never stops the run, whatever tol is: with tol above
+    # every change, the run stops at the first accepted trial
+    first_acc = acc.index(True)
+    res2 = O.lm_fit(p.Y, p.init, mu0=1.0, max_iter=30, tol=10.0)
+    assert res2.stop == "tol" and res2.iters == first_acc + 1
+
+
+def test_lm_fit_mu_max_and_max_iter_stops():
+    p = synth.make_problem(43, (5, 6, 7), 2, snr_db=20)
+    res = O.lm_fit(p.Y, p.init, mu0=1.0, max_iter=7, tol=0.0)
+    assert res.stop == "max_iter" and res.iters == 7
+    # mu_max below mu_0 after any damping growth: the first rejected trial, or
+    # an accepted one whose mu stays above mu_max, ends the run
+    res = O.lm_fit(p.Y, p.init, mu0=1e6, max_iter=50, tol=0.0, mu_max=1e6)
+    assert res.stop == "mu_max" and res.mu > 1e6
+
 # ------------------------------------------------------------------ generator
 
 

@@ -59,7 +59,7 @@ def test_noalloc_gram_matches_cp_gram_twice(cp, dims, R):
 
 
 def test_noalloc_rejects_oversized_shape(cp):
-    # ceil(I/8) rows blocks * (R(R+1)/2 + R^2) doubles exceeds the 2^18-double scratch
+    # ceil(I/8) row blocks * R(R+1)/2 doubles exceeds the 2^18-double scratch
     shape = cp.make_shape((20000, 20000), 32, "f64")
     a = torch.zeros(1, dtype=torch.float64, device="cuda")
     C = torch.zeros(2 * 32 * 32, dtype=torch.float64, device="cuda")
