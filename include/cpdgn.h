@@ -74,7 +74,10 @@ enum cp_code {
 /* core-system solver of cp_dgn_solve / cp_dgn_step */
 enum cp_core_mode {
   CP_CORE_F64 = 0,    /* float64 Cholesky of the core system */
-  CP_CORE_MIXED = 1   /* float32 Gauss-Jordan inverse + float64 iterative refinement */
+  CP_CORE_MIXED = 1   /* float32 Gauss-Jordan inverse + float64 iterative refinement;
+                         a trial whose refinement does not reach 1e-14 ||b|| (an
+                         ill-conditioned core) is solved by the float64 Cholesky
+                         instead (cp_status.core_f64 = 1) */
 };
 
 /* stop reasons in cp_status.stop */
@@ -130,7 +133,10 @@ typedef struct cp_status {
   int32_t last_accepted;   /* 1 if the last trial was accepted */
   int32_t info;            /* first non-positive pivot (1-based) of the last factorisation */
   int32_t refine_sweeps;   /* refinement residuals formed by the last CP_CORE_MIXED solve */
-  int32_t reserved_i[1];
+  int32_t core_f64;        /* 1 if the last CP_CORE_MIXED trial solved its core system
+                              by the float64 Cholesky fallback (the refinement did
+                              not reach 1e-14 ||b||, or the float32 inverse met a
+                              bad pivot); 0 otherwise */
 } cp_status;
 
 typedef struct cp_state cp_state;   /* opaque host handle */
@@ -214,8 +220,12 @@ int cp_dgn_core_build(const cp_shape* shape, const double* a, const double* m,
  * (Theorem 1, Eq. inverse_f1a):  f = K w - K S core^{-1} S^T K w, by float64
  * Cholesky.  core (in/out): on return holds its lower Cholesky factor (the
  * upper triangle is left unspecified).  info (device int) receives 0, or the
- * 1-based index of the first non-positive pivot.  a and mu must be those
- * given to cp_dgn_core_build. */
+ * 1-based index of the first non-positive pivot (N R^2 + 1 if a bounded
+ * wait of the factorisation ran out; the device's timeout count then also
+ * grows).  a and mu must be those given to cp_dgn_core_build.  The
+ * factorisation is one persistent launch whose CTAs (at most one per SM)
+ * meet at grid barriers, so it should not share the GPU with other work
+ * that fills every SM. */
 int cp_dgn_solve(const cp_shape* shape, const double* a, const double* mu, double* core,
                  const double* w, double* f, int* info, void* ws, size_t ws_bytes,
                  void* stream);

@@ -56,7 +56,7 @@ class Status(ctypes.Structure):
                 ("refine_resid", ctypes.c_double), ("reserved_d", ctypes.c_double * 3),
                 ("iters", ctypes.c_int32), ("accepted", ctypes.c_int32), ("stop", ctypes.c_int32),
                 ("error", ctypes.c_int32), ("last_accepted", ctypes.c_int32), ("info", ctypes.c_int32),
-                ("refine_sweeps", ctypes.c_int32), ("reserved_i", ctypes.c_int32 * 1)]
+                ("refine_sweeps", ctypes.c_int32), ("core_f64", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

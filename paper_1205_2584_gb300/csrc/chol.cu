@@ -1,258 +1,407 @@
-// Blocked right-looking Cholesky of the N R^2 x N R^2 core system and the two
-// triangular solves, for T = double (float64 core mode) and T = float (mixed
-// mode, refined in float64 by the caller).  Column-major, lower triangle;
-// the upper triangle is never read and is left unspecified.
+// Float64 Cholesky factorisation of the N R^2 x N R^2 core system and the two
+// triangular solves of the core solve (Theorem 1, Eq. inverse_f1a, in the
+// symmetric positive definite form core = I + S^T K S).  Column-major, lower
+// triangle; the upper triangle is never read and is left unspecified.
 //
-// Per panel step k0 (block width NB):
-//   k_chol_panel : every CTA factors the diagonal block in shared memory;
-//                  CTA 0 writes it, CTA b > 0 solves row block b of the panel
-//                  (X <- X L_kk^{-T}) and writes it;
-//   k_chol_update: trailing update A_ij -= L_ik L_jk^T over 64 x 64 tiles of
-//                  the lower triangle.
+// GB300 runs float64 at 2 multiply-adds per clock per SM with ~40 cycles of
+// latency, so the design spreads every panel's work over all SMs and keeps
+// the number of launches small:
+//
+//  k_chol64 (one persistent launch, one CTA per SM, blocked right-looking
+//  with 32-wide panels).  Per panel k:
+//    phase A  every CTA factors the 32 x 32 diagonal tile in shared memory
+//             (one warp, lane = row, the pivot's reciprocal square root
+//             shared through a shuffle), and solves its share of the panel's
+//             rows X <- X L_kk^{-T} (one warp per row, lane = column);
+//    phase B  the trailing update A_ij -= L_ik L_jk^T over 32 x 32 tiles of
+//             the lower triangle, tiles dealt round-robin to the CTAs;
+//  separated by grid barriers (an arrival counter and a generation word in
+//  the workspace, every wait bounded).  Finally each diagonal tile's inverse
+//  L_cc^{-1} is written to `dinv` for the solves.
+//
+//  k_trsv64 (one launch per direction, dataflow).  CTA t takes block row
+//  c = t (forward) or nb - 1 - t (backward) from an atomic ticket, so a CTA
+//  only ever waits on block rows taken by CTAs that started before it; it
+//  accumulates the off-diagonal products of the block rows already published
+//  (each wait bounded), multiplies by L_cc^{-1} (or its transpose) and
+//  publishes its block with a flag.
+//
 // A non-positive or non-finite pivot records its 1-based index in *info
-// (first one wins) and the factorisation continues with NaNs; nothing traps.
+// (first one wins) and the factorisation continues with the pivot replaced
+// by 1, so no NaN is produced; a wait that runs out sets the abort word, adds
+// one to the caller's timeout counter, makes every CTA return, and sets *info
+// to n + 1 so that the result is never used as a factor.
 #include "common.cuh"
 
 namespace cpdgn {
 
-constexpr int NB = 32;        // panel width
-constexpr int TB = 64;        // trailing-update tile
-constexpr int PT = 256;       // threads of the panel / update kernels
+constexpr int CB = 32;                           // panel / tile width
+constexpr int CT = 256;                          // threads per CTA (8 warps)
+constexpr uint64_t kWaitNs = 2000000000ull;      // every wait gives up after 2 s
 
-template <typename T>
-__device__ void factor_diag(T (*D)[NB + 1], int kb, int* bad) {
-  const int tid = threadIdx.x;
-  for (int c = 0; c < kb; ++c) {
-    __syncthreads();
-    const T piv = D[c][c];
-    if (tid == 0 && (!(piv > T(0)) || !isfinite(double(piv))) && *bad == 0) *bad = c + 1;
-    const T dc = sqrt(piv);
-    __syncthreads();
-    if (tid == 0) D[c][c] = dc;
-    for (int i = c + 1 + tid; i < kb; i += PT) D[i][c] /= dc;
-    __syncthreads();
-    const int m = kb - c - 1;   // trailing size
-    for (int e = tid; e < m * m; e += PT) {
-      const int i = c + 1 + e % m, l = c + 1 + e / m;
-      if (l <= i) D[i][l] -= D[i][c] * D[l][c];
-    }
-  }
-  __syncthreads();
+__device__ __forceinline__ uint64_t chol_gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PT) k_chol_panel(T* A, int64_t n, int64_t k0, int* info,
-                                                   const int* skip) {
+// Sync words of the factorisation and the solves, in the workspace.  Zeroed
+// (cudaMemsetAsync) before every launch that uses them.
+struct CholSync {
+  unsigned count;        // grid barrier: CTAs arrived
+  unsigned gen;          // grid barrier: generation
+  int abort;             // set when a wait ran out
+  int ticket;            // block-row ticket of a solve
+  int flags[1];          // solve: block row published (nb entries)
+};
+
+size_t chol64_sync_bytes(int64_t n) { return sizeof(CholSync) + sizeof(int) * size_t((n + CB - 1) / CB); }
+size_t chol64_dinv_bytes(int64_t n) { return sizeof(double) * CB * CB * size_t((n + CB - 1) / CB); }
+
+__device__ void chol_fail(CholSync* sy, int* info, int64_t n, int* tmo) {
+  if (atomicExch(&sy->abort, 1) == 0) {
+    if (tmo) atomicAdd(tmo, 1);
+  }
+  if (info) atomicExch(info, int(n + 1));
+}
+
+// Grid-wide barrier of the G co-resident CTAs of k_chol64; false if aborted.
+__device__ bool grid_barrier(CholSync* sy, unsigned G, unsigned& epoch, int* info, int64_t n, int* tmo) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned target = epoch + 1;
+    int ok = 1;
+    if (atomicAdd(&sy->count, 1u) == G - 1) {
+      sy->count = 0;                 // nobody arrives again before gen moves
+      __threadfence();
+      atomicExch(&sy->gen, target);
+    } else {
+      const uint64_t t0 = chol_gtimer();
+      for (;;) {
+        if (int(*reinterpret_cast<volatile unsigned*>(&sy->gen) - target) >= 0) break;
+        if (*reinterpret_cast<volatile int*>(&sy->abort)) { ok = 0; break; }
+        if (chol_gtimer() - t0 > kWaitNs) {
+          chol_fail(sy, info, n, tmo);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    epoch = target;
+    s_ok = ok && !*reinterpret_cast<volatile int*>(&sy->abort);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Factor the kb x kb tile D (lower part) in place; warp 0 only, lane = row.
+// rinv[j] = 1 / L_jj.  Returns (lane 0) the first bad pivot, 1-based, or 0.
+__device__ int factor_tile(double (*D)[CB + 1], int kb, double* rinv) {
+  const int lane = threadIdx.x & 31;
+  double a[CB];
+#pragma unroll
+  for (int j = 0; j < CB; ++j)
+    a[j] = (lane < kb && j < kb) ? (j <= lane ? D[lane][j] : 0.0) : (lane == j ? 1.0 : 0.0);
+  int bad = 0;
+#pragma unroll
+  for (int j = 0; j < CB; ++j) {
+    double piv = __shfl_sync(0xffffffffu, a[j], j);
+    if (!(piv > 0.0) || !isfinite(piv)) {
+      if (bad == 0 && j < kb) bad = j + 1;
+      piv = 1.0;
+      if (lane == j) a[j] = 1.0;
+    }
+    const double r = rsqrt(piv);                 // every lane: 1 / L_jj
+    const double lij = a[j] * r;                 // lane > j: L_ij; lane j: L_jj
+    a[j] = lij;
+    if (lane == 0) rinv[j] = r;
+#pragma unroll
+    for (int l = j + 1; l < CB; ++l) {
+      const double llj = __shfl_sync(0xffffffffu, lij, l);
+      if (l <= lane) a[l] = fma(-lij, llj, a[l]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CB; ++j)
+    if (j <= lane) D[lane][j] = a[j];
+  return bad;
+}
+
+__global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* dinv, int* info, CholSync* sy,
+                                               int* tmo, const int* skip) {
   if (skip && *skip) return;
-  __shared__ T D[NB][NB + 1];
-  __shared__ T X[NB][NB + 1];
-  __shared__ int bad;
-  const int tid = threadIdx.x;
-  const int kb = int((n - k0) < NB ? (n - k0) : NB);
-  if (tid == 0) bad = 0;
-  for (int e = tid; e < kb * kb; e += PT) {
-    const int i = e % kb, l = e / kb;
-    D[i][l] = A[(k0 + i) + n * (k0 + l)];
-  }
-  factor_diag<T>(D, kb, &bad);
-  if (blockIdx.x == 0) {
-    if (tid == 0 && bad && info) atomicCAS(info, 0, int(k0) + bad);
-    for (int e = tid; e < kb * kb; e += PT) {
-      const int i = e % kb, l = e / kb;
-      if (i >= l) A[(k0 + i) + n * (k0 + l)] = D[i][l];
-    }
-    return;
-  }
-  const int64_t i0 = k0 + int64_t(blockIdx.x) * NB;
-  if (i0 >= n) return;
-  const int ib = int((n - i0) < NB ? (n - i0) : NB);
-  for (int e = tid; e < ib * kb; e += PT) {
-    const int i = e % ib, l = e / ib;
-    X[i][l] = A[(i0 + i) + n * (k0 + l)];
-  }
-  __syncthreads();
-  // X <- X D^{-T}: column c of the result depends on columns < c
-  for (int c = 0; c < kb; ++c) {
-    for (int i = tid; i < ib; i += PT) X[i][c] /= D[c][c];
-    __syncthreads();
-    const int m = kb - c - 1;
-    for (int e = tid; e < ib * m; e += PT) {
-      const int i = e % ib, l = c + 1 + e / ib;
-      X[i][l] -= X[i][c] * D[l][c];
+  __shared__ double D[CB][CB + 1];
+  __shared__ double rinv[CB];
+  __shared__ double Pi[CB][CB + 1], Pj[CB][CB + 1];
+  __shared__ int s_bad;
+  const unsigned G = gridDim.x;
+  const int cta = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nb = int((n + CB - 1) / CB);
+  unsigned epoch = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t k0 = int64_t(k) * CB;
+    const int kb = int((n - k0) < CB ? (n - k0) : CB);
+    // ---- phase A: diagonal tile and panel solve ----
+    for (int e = tid; e < CB * CB; e += CT) {
+      const int i = e % CB, j = e / CB;
+      D[i][j] = (i < kb && j <= i) ? A[(k0 + i) + n * (k0 + j)] : 0.0;
     }
     __syncthreads();
+    if (warp == 0) {
+      const int bad = factor_tile(D, kb, rinv);
+      if (lane == 0) s_bad = bad;
+    }
+    __syncthreads();
+    for (int64_t r = k0 + kb + int64_t(cta) * 8 + warp; r < n; r += int64_t(G) * 8) {
+      double x = lane < kb ? A[r + n * (k0 + lane)] : 0.0;
+#pragma unroll 8
+      for (int j = 0; j < kb; ++j) {
+        const double xj = __shfl_sync(0xffffffffu, x, j) * rinv[j];
+        if (lane == j) x = xj;
+        else if (lane > j) x = fma(-xj, D[lane][j], x);
+      }
+      if (lane < kb) A[r + n * (k0 + lane)] = x;
+    }
+    // every CTA has read tile (k, k) of A; CTA 0 may now store L_kk there
+    if (!grid_barrier(sy, G, epoch, info, n, tmo)) return;
+    if (cta == 0) {
+      if (tid == 0 && s_bad && info) atomicCAS(info, 0, int(k0) + s_bad);
+      for (int e = tid; e < kb * kb; e += CT) {
+        const int i = e % kb, j = e / kb;
+        if (j <= i) A[(k0 + i) + n * (k0 + j)] = D[i][j];
+      }
+    }
+    if (k + 1 == nb) break;
+    // ---- phase B: trailing update of the lower triangle ----
+    const int t = nb - k - 1;
+    const int64_t T = int64_t(t) * (t + 1) / 2;
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int64_t e = cta; e < T; e += G) {
+      int ti = int((sqrt(8.0 * double(e) + 1.0) - 1.0) * 0.5);
+      while (int64_t(ti + 1) * (ti + 2) / 2 <= e) ++ti;
+      while (int64_t(ti) * (ti + 1) / 2 > e) --ti;
+      const int tj = int(e - int64_t(ti) * (ti + 1) / 2);
+      const int64_t r0 = int64_t(k + 1 + ti) * CB, c0 = int64_t(k + 1 + tj) * CB;
+      for (int q = tid; q < CB * CB; q += CT) {
+        const int i = q % CB, l = q / CB;
+        Pi[i][l] = (r0 + i < n) ? A[(r0 + i) + n * (k0 + l)] : 0.0;
+        Pj[i][l] = (c0 + i < n) ? A[(c0 + i) + n * (k0 + l)] : 0.0;
+      }
+      __syncthreads();
+      double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll 8
+      for (int l = 0; l < CB; ++l) {
+        const double a0 = Pi[tx][l], a1 = Pi[tx + 16][l], b0 = Pj[ty][l], b1 = Pj[ty + 16][l];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const int64_t r = r0 + tx + 16 * u, c = c0 + ty + 16 * v;
+          if (r < n && c < n && r >= c) A[r + n * c] -= acc[u][v];
+        }
+      __syncthreads();
+    }
+    if (!grid_barrier(sy, G, epoch, info, n, tmo)) return;
   }
-  for (int e = tid; e < ib * kb; e += PT) {
-    const int i = e % ib, l = e / ib;
-    A[(i0 + i) + n * (k0 + l)] = X[i][l];
+  // the last diagonal tile, stored by CTA 0 after the last barrier, is read below
+  if (!grid_barrier(sy, G, epoch, info, n, tmo)) return;
+  // ---- inverses of the diagonal tiles: warps 0-2 of each CTA, one tile each ----
+  if (warp < 3) {
+    double (*Lt)[CB + 1] = warp == 0 ? D : (warp == 1 ? Pi : Pj);
+    for (int c = cta * 3 + warp; c < nb; c += int(G) * 3) {
+      const int64_t c0 = int64_t(c) * CB;
+      const int cb = int((n - c0) < CB ? (n - c0) : CB);
+      for (int q = lane; q < CB * CB; q += 32) {
+        const int i = q % CB, l = q / CB;
+        Lt[i][l] = (i < cb && l < cb && l <= i) ? A[(c0 + i) + n * (c0 + l)] : (i == l ? 1.0 : 0.0);
+      }
+      __syncwarp();
+      double* Xc = dinv + int64_t(c) * CB * CB;
+      // lane j: column j of L^{-1} by forward substitution, x_i = 0 for i < j
+      double x[CB];
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        if (i < lane) {
+          x[i] = 0.0;
+        } else if (i == lane) {
+          x[i] = 1.0 / Lt[i][i];
+        } else {
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+          for (int l = 0; l < i; l += 4) {
+            s0 = fma(Lt[i][l], x[l], s0);
+            if (l + 1 < i) s1 = fma(Lt[i][l + 1], x[l + 1], s1);
+            if (l + 2 < i) s2 = fma(Lt[i][l + 2], x[l + 2], s2);
+            if (l + 3 < i) s3 = fma(Lt[i][l + 3], x[l + 3], s3);
+          }
+          x[i] = -((s0 + s1) + (s2 + s3)) / Lt[i][i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < CB; ++i) Xc[i + CB * lane] = x[i];
+      __syncwarp();
+    }
   }
 }
 
-// Trailing update of the lower triangle of A[k1:n, k1:n], k1 = k0 + kb.
-template <typename T>
-__global__ void __launch_bounds__(PT) k_chol_update(T* A, int64_t n, int64_t k0, int kb,
-                                                    const int* skip) {
+// Forward (L z = b) or backward (L^T y = b) solve with the factor and the
+// diagonal-tile inverses of k_chol64.  One CTA per block row (ticket order).
+__global__ void __launch_bounds__(CT) k_trsv64(const double* L, const double* dinv, int64_t n, const double* b,
+                                               double* x, int backward, CholSync* sy, int* info, int* tmo,
+                                               const int* skip) {
   if (skip && *skip) return;
-  __shared__ T Pi[TB][NB + 1];
-  __shared__ T Pj[TB][NB + 1];
-  const int64_t k1 = k0 + kb;
-  // tile (ti, tj), ti >= tj, from the linear block index
-  int ti = 0;
-  {
-    const int b = blockIdx.x;
-    ti = int((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
-    while ((ti + 1) * (ti + 2) / 2 <= b) ++ti;
-    while (ti * (ti + 1) / 2 > b) --ti;
+  __shared__ int s_c;
+  __shared__ double part[8][CB];
+  __shared__ double rr[CB];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nb = int((n + CB - 1) / CB);
+  if (tid == 0) s_c = atomicAdd(&sy->ticket, 1);
+  __syncthreads();
+  const int t = s_c;
+  if (t >= nb) return;
+  const int c = backward ? nb - 1 - t : t;
+  const int64_t c0 = int64_t(c) * CB;
+  const int cb = int((n - c0) < CB ? (n - c0) : CB);
+  double acc = 0.0;                // forward: row c0 + lane; backward: outputs 4 warp .. 4 warp + 3
+  double accb[4] = {0.0, 0.0, 0.0, 0.0};
+  bool ok = true;
+  const int j_lo = backward ? c + 1 : 0, j_hi = backward ? nb : c;
+  for (int jj = j_lo; jj < j_hi && ok; ++jj) {
+    const int j = backward ? (nb - 1 - (jj - j_lo)) : jj;     // wait in publication order
+    if (lane == 0) {
+      const uint64_t t0 = chol_gtimer();
+      for (;;) {
+        if (*reinterpret_cast<volatile int*>(&sy->flags[j])) break;
+        if (*reinterpret_cast<volatile int*>(&sy->abort)) { ok = false; break; }
+        if (chol_gtimer() - t0 > kWaitNs) {
+          chol_fail(sy, info, n, tmo);
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (!ok) break;
+    __threadfence();
+    const int64_t j0 = int64_t(j) * CB;
+    const int jb = int((n - j0) < CB ? (n - j0) : CB);
+    if (!backward) {
+      // acc(row c0 + lane) += sum over this warp's 4 columns l of L[c0 + lane, j0 + l] x[j0 + l]
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int l = 4 * warp + q;
+        if (l < jb && lane < cb) acc = fma(L[(c0 + lane) + n * (j0 + l)], __ldcg(x + j0 + l), acc);
+      }
+    } else {
+      // output i = 4 warp + q: sum over rows l (= lane) of L[j0 + l, c0 + i] x[j0 + l]
+      const double xl = lane < jb ? __ldcg(x + j0 + lane) : 0.0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * warp + q;
+        if (i < cb && lane < jb) accb[q] = fma(L[(j0 + lane) + n * (c0 + i)], xl, accb[q]);
+      }
+    }
   }
-  const int tj = blockIdx.x - ti * (ti + 1) / 2;
-  const int64_t r0 = k1 + int64_t(ti) * TB, c0 = k1 + int64_t(tj) * TB;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < TB * kb; e += PT) {
-    const int i = e % TB, l = e / TB;
-    const int64_t ri = r0 + i, cj = c0 + i;
-    Pi[i][l] = (ri < n) ? A[ri + n * (k0 + l)] : T(0);
-    Pj[i][l] = (cj < n) ? A[cj + n * (k0 + l)] : T(0);
+  if (!backward) {
+    part[warp][lane] = acc;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double v = accb[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) part[0][4 * warp + q] = v;
+    }
   }
   __syncthreads();
-  const int tx = tid % 16, ty = tid / 16;
-  T acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-  for (int l = 0; l < kb; ++l) {
-    T a[4], b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) a[u] = Pi[tx + 16 * u][l];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) b[v] = Pj[ty + 16 * v][l];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int64_t r = r0 + tx + 16 * u, c = c0 + ty + 16 * v;
-      if (r < n && c < n && r >= c) A[r + n * c] -= acc[u][v];
+  if (*reinterpret_cast<volatile int*>(&sy->abort)) return;
+  if (tid < CB) {
+    double s = 0.0;
+    if (!backward) {
+      for (int w = 0; w < 8; ++w) s += part[w][tid];
+    } else {
+      s = part[0][tid];
     }
+    rr[tid] = tid < cb ? b[c0 + tid] - s : 0.0;
+  }
+  __syncthreads();
+  if (tid < CB) {
+    const double* Xc = dinv + int64_t(c) * CB * CB;
+    double s0 = 0.0, s1 = 0.0;
+    if (!backward) {
+#pragma unroll 8
+      for (int l = 0; l < CB; l += 2) {
+        s0 = fma(Xc[tid + CB * l], rr[l], s0);
+        s1 = fma(Xc[tid + CB * (l + 1)], rr[l + 1], s1);
+      }
+    } else {
+#pragma unroll 8
+      for (int l = 0; l < CB; l += 2) {
+        s0 = fma(Xc[l + CB * tid], rr[l], s0);
+        s1 = fma(Xc[(l + 1) + CB * tid], rr[l + 1], s1);
+      }
+    }
+    if (tid < cb) x[c0 + tid] = s0 + s1;
+    __threadfence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    atomicExch(&sy->flags[c], 1);
   }
 }
 
-template <typename T>
-int chol_factor(T* A, int64_t n, int* info, const int* skip, cudaStream_t s) {
-  for (int64_t k0 = 0; k0 < n; k0 += NB) {
-    const int kb = int((n - k0) < NB ? (n - k0) : NB);
-    const int64_t nbr = (n - k0 + NB - 1) / NB;
-    k_chol_panel<T><<<unsigned(nbr), PT, 0, s>>>(A, n, k0, info, skip);
-    const int64_t rest = n - k0 - kb;
-    if (rest > 0) {
-      const int64_t nt = (rest + TB - 1) / TB;
-      k_chol_update<T><<<unsigned(nt * (nt + 1) / 2), PT, 0, s>>>(A, n, k0, kb, skip);
-    }
+static int chol64_grid() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1)
+      sms = kSMs;
   }
+  return sms;
+}
+
+// Factor A = L L^T in place (lower triangle), L_cc^{-1} into dinv.
+// sync: chol64_sync_bytes(n) bytes of workspace; tmo: device timeout counter.
+int chol64_factor(double* A, int64_t n, double* dinv, int* info, void* sync, int* tmo, const int* skip,
+                  cudaStream_t s) {
+  if (n < 1) return CP_EINVAL;
+  CholSync* sy = static_cast<CholSync*>(sync);
+  if (cudaMemsetAsync(sy, 0, sizeof(CholSync), s) != cudaSuccess) return CP_ECUDA;
+  const int nb = int((n + CB - 1) / CB);
+  int G = chol64_grid();
+  // enough CTAs for the widest phase, at most one per SM (they must all be
+  // resident at once for the grid barrier)
+  int64_t want = int64_t(nb) * (nb - 1) / 2;
+  const int64_t rows = (n + 7) / 8;
+  if (rows > want) want = rows;
+  if (want < 1) want = 1;
+  if (G > want) G = int(want);
+  k_chol64<<<G, CT, 0, s>>>(A, n, dinv, info, sy, tmo, skip);
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
-template int chol_factor<double>(double*, int64_t, int*, const int*, cudaStream_t);
-template int chol_factor<float>(float*, int64_t, int*, const int*, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// Triangular solves, one launch per block of TS rows.
-//   forward : L z = x   (x is consumed: rows below the block are updated)
-//   backward: L^T y = x (x is consumed: rows above the block are updated)
-// TX is the type of the right-hand side / solution vectors.
-// ---------------------------------------------------------------------------
-constexpr int TS = 64;
-constexpr int TRows = 256;   // rows updated per CTA
-
-template <typename T, typename TX>
-__global__ void __launch_bounds__(TS) k_trsv_fwd(const T* L, int64_t n, int64_t k0, TX* x, TX* z,
-                                                 const int* skip) {
-  if (skip && *skip) return;
-  __shared__ T D[TS][TS + 1];
-  __shared__ T zk[TS];
-  const int tid = threadIdx.x;
-  const int kb = int((n - k0) < TS ? (n - k0) : TS);
-  for (int e = tid; e < kb * kb; e += TS) {
-    const int i = e % kb, l = e / kb;
-    D[i][l] = (i >= l) ? L[(k0 + i) + n * (k0 + l)] : T(0);
-  }
-  if (tid < kb) zk[tid] = T(x[k0 + tid]);
-  __syncthreads();
-  for (int p = 0; p < kb; ++p) {
-    const T zp = zk[p] / D[p][p];
-    __syncthreads();
-    if (tid == p) zk[p] = zp;
-    if (tid > p && tid < kb) zk[tid] -= D[tid][p] * zp;
-    __syncthreads();
-  }
-  if (blockIdx.x == 0) {
-    if (tid < kb) z[k0 + tid] = TX(zk[tid]);
-    return;
-  }
-  const int64_t rbeg = k0 + kb + int64_t(blockIdx.x - 1) * TRows;
-  for (int64_t r = rbeg + tid; r < rbeg + TRows && r < n; r += TS) {
-    T s = T(0);
-    for (int l = 0; l < kb; ++l) s = fma(L[r + n * (k0 + l)], zk[l], s);
-    x[r] = TX(T(x[r]) - s);
-  }
-}
-
-template <typename T, typename TX>
-__global__ void __launch_bounds__(TS) k_trsv_bwd(const T* L, int64_t n, int64_t k0, TX* x, TX* y,
-                                                 const int* skip) {
-  if (skip && *skip) return;
-  __shared__ T D[TS][TS + 1];
-  __shared__ T yk[TS];
-  const int tid = threadIdx.x;
-  const int kb = int((n - k0) < TS ? (n - k0) : TS);
-  for (int e = tid; e < kb * kb; e += TS) {
-    const int i = e % kb, l = e / kb;
-    D[i][l] = (i >= l) ? L[(k0 + i) + n * (k0 + l)] : T(0);
-  }
-  if (tid < kb) yk[tid] = T(x[k0 + tid]);
-  __syncthreads();
-  for (int p = kb - 1; p >= 0; --p) {
-    const T yp = yk[p] / D[p][p];
-    __syncthreads();
-    if (tid == p) yk[p] = yp;
-    if (tid < p) yk[tid] -= D[p][tid] * yp;
-    __syncthreads();
-  }
-  if (blockIdx.x == 0) {
-    if (tid < kb) y[k0 + tid] = TX(yk[tid]);
-    return;
-  }
-  // rows r < k0: x[r] -= sum_l L[k0 + l, r] y_l
-  const int64_t rbeg = int64_t(blockIdx.x - 1) * TRows;
-  for (int64_t r = rbeg + tid; r < rbeg + TRows && r < k0; r += TS) {
-    T s = T(0);
-    for (int l = 0; l < kb; ++l) s = fma(L[(k0 + l) + n * r], yk[l], s);
-    x[r] = TX(T(x[r]) - s);
-  }
-}
-
-// y = (L L^T)^{-1} x; x is destroyed, tmp has length n.
-template <typename T, typename TX>
-int chol_solve(const T* L, int64_t n, TX* x, TX* tmp, TX* y, const int* skip, cudaStream_t s) {
-  for (int64_t k0 = 0; k0 < n; k0 += TS) {
-    const int kb = int((n - k0) < TS ? (n - k0) : TS);
-    const int64_t rest = n - k0 - kb;
-    const int64_t g = 1 + (rest + TRows - 1) / TRows;
-    k_trsv_fwd<T, TX><<<unsigned(g), TS, 0, s>>>(L, n, k0, x, tmp, skip);
-  }
-  const int64_t last = ((n - 1) / TS) * TS;
-  for (int64_t k0 = last; k0 >= 0; k0 -= TS) {
-    const int64_t g = 1 + (k0 + TRows - 1) / TRows;
-    k_trsv_bwd<T, TX><<<unsigned(g), TS, 0, s>>>(L, n, k0, tmp, y, skip);
-  }
+// y = (L L^T)^{-1} b with the factor of chol64_factor; z: n doubles of scratch.
+int chol64_solve(const double* L, const double* dinv, int64_t n, const double* b, double* z, double* y,
+                 void* sync, int* info, int* tmo, const int* skip, cudaStream_t s) {
+  CholSync* sy = static_cast<CholSync*>(sync);
+  const int nb = int((n + CB - 1) / CB);
+  if (cudaMemsetAsync(sy, 0, chol64_sync_bytes(n), s) != cudaSuccess) return CP_ECUDA;
+  k_trsv64<<<nb, CT, 0, s>>>(L, dinv, n, b, z, 0, sy, info, tmo, skip);
+  if (cudaMemsetAsync(sy, 0, chol64_sync_bytes(n), s) != cudaSuccess) return CP_ECUDA;
+  k_trsv64<<<nb, CT, 0, s>>>(L, dinv, n, z, y, 1, sy, info, tmo, skip);
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
-template int chol_solve<double, double>(const double*, int64_t, double*, double*, double*, const int*,
-                                        cudaStream_t);
-template int chol_solve<float, float>(const float*, int64_t, float*, float*, float*, const int*,
-                                      cudaStream_t);
 
 }  // namespace cpdgn

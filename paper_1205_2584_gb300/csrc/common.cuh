@@ -90,6 +90,8 @@ enum Seg {
   S_PART,         // partial sums of the update kernel
   S_SCAL,         // small scalars and flags (doubles)
   S_INFO,         // ints
+  S_DINV,         // ceil(N R^2 / 32) x 32 x 32 double: inverses of the Cholesky factor's diagonal tiles
+  S_SYNC,         // grid-barrier and dataflow words of the float64 Cholesky and solves
   // state
   S_STATUS,       // cp_status
   S_M,            // R T  MTTKRP at the current factors
@@ -133,6 +135,11 @@ inline void make_layout(const Dims& d, int core_mode, int with_state, Layout* L)
   sz[S_PART] = size_t(update_ctas(d)) * (1 + d.R) * dbl;
   sz[S_SCAL] = 64 * dbl;
   sz[S_INFO] = 64 * sizeof(int);
+  {
+    const size_t nbk = size_t((d.ncore + 31) / 32);
+    sz[S_DINV] = nbk * 32 * 32 * dbl;
+    sz[S_SYNC] = 64 + nbk * sizeof(int);
+  }
   if (with_state) {
     sz[S_STATUS] = sizeof(cp_status);
     sz[S_M] = sz[S_MT] = sz[S_AT] = sz[S_DELTA] = size_t(d.T) * d.R * dbl;

@@ -46,10 +46,10 @@ int launch_apply_S(const Dims& d, const double* LC, const double* U, const doubl
 int launch_apply_ST(const Dims& d, const double* LC, const double* U, const double* Gnm, const double* x,
                     int kx, const double* b, const double* y, double* out, double* kw, double* norm2,
                     const int* skip, cudaStream_t s);
-template <typename T>
-int chol_factor(T* A, int64_t n, int* info, const int* skip, cudaStream_t s);
-template <typename T, typename TX>
-int chol_solve(const T* L, int64_t n, TX* x, TX* tmp, TX* y, const int* skip, cudaStream_t s);
+int chol64_factor(double* A, int64_t n, double* dinv, int* info, void* sync, int* tmo, const int* skip,
+                  cudaStream_t s);
+int chol64_solve(const double* L, const double* dinv, int64_t n, const double* b, double* z, double* y,
+                 void* sync, int* info, int* tmo, const int* skip, cudaStream_t s);
 template <typename T>
 int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const int* skip, cudaStream_t s,
               cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result);
@@ -61,7 +61,11 @@ int launch_gemv_acc(const float* X, int64_t n, const double* r, double* y, const
 enum { SC_R2T = 0, SC_YN2 = 1, SC_R2 = 2, SC_REFN = 3, SC_NRM = 8 };   // SC_NRM..: ||b||^2, ||res_k||^2
 constexpr int kMaxRefine = 48;
 // int slots inside S_INFO
-enum { IN_INFO = 0, IN_COMMIT = 1, IN_ZERO = 2, IN_RDONE = 3, IN_TOBASE = 4 };
+// IN_INFO: first failed pivot of the trial (per-mode factors or the float64
+// core factor: the trial is rejected); IN_INFO32: first failed pivot of the
+// float32 core inverse (the mixed solve then falls back to float64);
+// IN_SKIP64: 1 unless the mixed solve needs its float64 fallback
+enum { IN_INFO = 0, IN_COMMIT = 1, IN_ZERO = 2, IN_RDONE = 3, IN_TOBASE = 4, IN_SKIP64 = 5, IN_INFO32 = 6 };
 
 struct Bufs {
   double *C, *Gnm, *Gall, *P, *LC, *U, *Gt, *w, *Kw, *b, *y, *Z, *res, *dcor, *f, *Wp;
@@ -71,6 +75,8 @@ struct Bufs {
   cp_status* status;
   double *m, *mt, *at, *delta, *scale, *mu;
   double* core64;
+  double* dinv;
+  void* sync;
 };
 
 static Bufs carve(const Layout& L, void* ws, int64_t ncore) {
@@ -108,6 +114,8 @@ static Bufs carve(const Layout& L, void* ws, int64_t ncore) {
   b.mu = reinterpret_cast<double*>(base + L.off[S_MU]);
   b.core64 = reinterpret_cast<double*>(base + L.off[S_CORE64]);
   b.core32b = b.core32 + size_t(ncore) * size_t(ncore);
+  b.dinv = reinterpret_cast<double*>(base + L.off[S_DINV]);
+  b.sync = base + L.off[S_SYNC];
   return b;
 }
 
@@ -119,6 +127,8 @@ __global__ void k_step_begin(int64_t nm, double* mt, double* scal, int* info, co
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i == 0) {
     info[IN_INFO] = 0;
+    info[IN_INFO32] = 0;
+    info[IN_SKIP64] = 1;
     info[IN_COMMIT] = 0;
     info[IN_RDONE] = (st->stop != CP_RUNNING) ? 1 : 0;
     scal[SC_R2T] = 0.0;
@@ -281,6 +291,7 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
     st->info = bad;
     st->refine_resid = rr_s;
     st->refine_sweeps = sweeps_s;
+    st->core_f64 = info[IN_SKIP64] ? 0 : 1;
     st->mu = mu;
     st->nu = nu;
     st->last_accepted = accept ? 1 : 0;
@@ -379,7 +390,7 @@ __global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double
   s.last_accepted = 0;
   s.info = 0;
   s.refine_sweeps = 0;
-  s.reserved_i[0] = 0;
+  s.core_f64 = 0;
   // a tensor or factors with NaN / Inf entries give a non-finite ||Y||^2 or
   // residual: nothing can be decided from them, so the run stops at once
   if (!isfinite(s.y_norm2) || !isfinite(s.resid2) || !isfinite(s.mu) || !(s.y_norm2 > 0.0)) {
@@ -409,14 +420,46 @@ static int core_rhs(const Dims& d, const Bufs& B, const int* skip, cudaStream_t 
   return launch_apply_ST(d, B.LC, B.U, B.Gnm, B.w, 1, nullptr, nullptr, B.b, B.Kw, B.scal + SC_NRM, skip, s);
 }
 
-static int solve_core(const Dims& d, const Bufs& B, const double* L64, const float* X32, int mode,
-                      int refine_iters, const int* skip, cudaStream_t s, bool rhs_ready = false) {
+// Decide whether the mixed solve must fall back to float64: skip64 = 1 when
+// the run has stopped or a refinement residual met ||r|| <= tol ||b|| (and
+// the float32 inverse had no bad pivot); else 0, and the float64 Cholesky
+// path below runs for this trial.
+__global__ void k_refine_verdict(const double* nrm, int K, double tol2, const int* stop, const int* info32,
+                                 int* skip64) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int out = 1;
+  if (*stop == CP_RUNNING) {
+    bool conv = !(nrm[0] > 0.0);                  // b = 0: y = 0 is exact
+    for (int k = 1; k <= K && !conv; ++k) {
+      const double v = nrm[k];
+      if (v > 0.0 && v <= tol2 * nrm[0]) conv = true;
+    }
+    if (*info32 != 0) conv = false;
+    out = conv ? 1 : 0;
+  }
+  *skip64 = out;
+}
+
+// y = core^{-1} b by the float64 Cholesky factor of `core` (lower triangle
+// filled here from the per-mode factors), skipped while *skip is set.
+static int solve_core_f64(const Dims& d, const Bufs& B, double* core, int* tmo, const int* skip, cudaStream_t s,
+                          bool fill) {
+  if (fill) CP_TRY(launch_core_fill<double>(d, B.LC, B.U, B.Wp, core, 0, skip, s));
+  CP_TRY(chol64_factor(core, d.ncore, B.dinv, B.info + IN_INFO, B.sync, tmo, skip, s));
+  CP_TRY(chol64_solve(core, B.dinv, d.ncore, B.b, B.dcor, B.y, B.sync, B.info + IN_INFO, tmo, skip, s));
+  return CP_OK;
+}
+
+// core64: the float64 core (CP_CORE_F64: filled and factored by the caller's
+// sequence here; CP_CORE_MIXED: storage for the fallback, may alias the
+// float32 buffers, which are dead by then).
+static int solve_core(const Dims& d, const Bufs& B, double* core64, const float* X32, int mode,
+                      int refine_iters, int* tmo, const int* skip, cudaStream_t s, bool rhs_ready = false) {
   const int64_t n = d.ncore;
   double* nrm = B.scal + SC_NRM;
   if (!rhs_ready) CP_TRY(core_rhs(d, B, skip, s));
   if (mode == CP_CORE_F64) {
-    CP_CUDA(cudaMemcpyAsync(B.res, B.b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CP_TRY((chol_solve<double, double>(L64, n, B.res, B.dcor, B.y, skip, s)));
+    CP_TRY(chol64_solve(core64, B.dinv, n, B.b, B.dcor, B.y, B.sync, B.info + IN_INFO, tmo, skip, s));
   } else {
     int* rdone = B.info + IN_RDONE;
     const int K = refine_iters < kMaxRefine ? refine_iters : kMaxRefine;
@@ -427,6 +470,12 @@ static int solve_core(const Dims& d, const Bufs& B, const double* L64, const flo
       CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Z, 1, B.b, B.y, B.res, nullptr, nrm + it, rdone, s));
       CP_TRY(launch_gemv_acc(X32, n, B.res, B.y, nrm, nrm + it, it > 1 ? nrm + it - 1 : nullptr, rdone, 1e-30,
                              rdone, s));
+    }
+    if (core64) {
+      // the refinement missed 1e-14 ||b|| (an ill-conditioned core: collinear
+      // factors at small mu) or the float32 inverse failed: float64 Cholesky
+      k_refine_verdict<<<1, 32, 0, s>>>(nrm, K, 1e-28, skip, B.info + IN_INFO32, B.info + IN_SKIP64);
+      CP_TRY(solve_core_f64(d, B, core64, tmo, B.info + IN_SKIP64, s, true));
     }
   }
   CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, skip, s));                        // Z = S y
@@ -509,9 +558,14 @@ extern "C" int cp_dgn_solve(const cp_shape* shape, const double* a, const double
   // S and K need the Gramians and the damped factors at (a, mu)
   CP_TRY(launch_gram(d, a, nullptr, B.gpart, B.C, nullptr, nullptr, nullptr, nullptr, s));
   CP_TRY(launch_mode_prep(d, B.C, nullptr, mu, B.Gnm, B.Gt, B.U, B.LC, nullptr, nullptr, nullptr, s));
-  CP_TRY(chol_factor<double>(core, d.ncore, info, nullptr, s));
+  int* tmo = nullptr;
+  CP_TRY(tc_timeout_counter(&tmo));
+  CP_TRY(chol64_factor(core, d.ncore, B.dinv, info, B.sync, tmo, nullptr, s));
   CP_CUDA(cudaMemcpyAsync(B.w, w, d.ncore * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CP_TRY(solve_core(d, B, core, nullptr, CP_CORE_F64, 0, nullptr, s));
+  CP_TRY(core_rhs(d, B, nullptr, s));
+  CP_TRY(chol64_solve(core, B.dinv, d.ncore, B.b, B.dcor, B.y, B.sync, info, tmo, nullptr, s));
+  CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, nullptr, s));
+  CP_TRY(launch_apply_K(d, B.Gnm, B.Z, B.Kw, B.f, nullptr, s));
   CP_CUDA(cudaMemcpyAsync(f, B.f, d.ncore * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return CP_OK;
 }
@@ -699,8 +753,8 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
   CP_TRY(launch_core_w(d, B.Gnm, B.LC, B.U, B.Wp, skip, s));
   if (st->o.core_mode == CP_CORE_F64) {
     CP_TRY(launch_core_fill<double>(d, B.LC, B.U, B.Wp, B.core64, 0, skip, s));
-    CP_TRY(chol_factor<double>(B.core64, d.ncore, B.info + IN_INFO, skip, s));
-    CP_TRY(solve_core(d, B, B.core64, nullptr, CP_CORE_F64, 0, skip, s));
+    CP_TRY(chol64_factor(B.core64, d.ncore, B.dinv, B.info + IN_INFO, B.sync, st->tmo, skip, s));
+    CP_TRY(solve_core(d, B, B.core64, nullptr, CP_CORE_F64, 0, st->tmo, skip, s));
   } else {
     // the right-hand side runs on a third stream while the core is filled and
     // inverted (the inversion's pivot chain leaves most SMs idle)
@@ -711,10 +765,12 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
     CP_TRY(launch_core_fill<float>(d, B.LC, B.U, B.Wp, B.core32, 1, skip, s));
     float* inv = nullptr;
     // the core's first R^2 x R^2 diagonal block is the identity
-    CP_TRY(gj_invert<float>(B.core32, B.core32b, B.pinv, d.ncore, d.RR, B.info + IN_INFO, skip, s, st->side,
+    CP_TRY(gj_invert<float>(B.core32, B.core32b, B.pinv, d.ncore, d.RR, B.info + IN_INFO32, skip, s, st->side,
                             st->ev_fork, st->ev_join, &inv));
     CP_CUDA(cudaStreamWaitEvent(s, st->ev_rhs_join, 0));
-    CP_TRY(solve_core(d, B, nullptr, inv, CP_CORE_MIXED, st->o.refine_iters, skip, s, true));
+    // the float64 fallback's core reuses the float32 buffers (2 n^2 floats = n^2 doubles)
+    CP_TRY(solve_core(d, B, reinterpret_cast<double*>(B.core32), inv, CP_CORE_MIXED, st->o.refine_iters, st->tmo,
+                      skip, s, true));
   }
   const int64_t nupd = update_ctas(d);
   k_update<<<unsigned(nupd), kUpdRows * 32, 0, s>>>(d, st->a, B.m, B.Gnm, B.Gt, B.f, mu, B.delta, B.at,
