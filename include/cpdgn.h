@@ -335,7 +335,12 @@ cp_status* cp_state_status(cp_state* st);
 int cp_als_sweep(cp_state* st, const void* Y, int sweeps, void* stream);
 
 /* Device address of an intermediate of the last trial, for inspection:
- * 0 = m (MTTKRP at the current factors, R*T), 1 = delta (last step, R*T),
+ * 0 = the pass output at the current factors (R*T): the gradient blocks
+ *     G_n = E_(n) (A^(N) (.) ... (.) A^(1) without A^(n)), E = Y - Y_hat, which
+ *     equal M_n - A^(n) Gamma^(n) (Sec. 4.6: g = J^T vec(E)) but are formed from
+ *     the residual tensor so that their rounding is relative to E, not to Y;
+ *     for a CP_BF16X2 tensor the MTTKRP M_n itself,
+ * 1 = delta (last step, R*T),
  * 2 = Gt (N R x R), 3 = w (N R^2), 4 = f (N R^2), 5 = a_trial (R*T).
  * Returns NULL for an unknown id. */
 double* cp_state_buffer(cp_state* st, int id);

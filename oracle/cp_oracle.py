@@ -496,3 +496,34 @@ def als_sweep(Y: np.ndarray, A: Sequence[np.ndarray],
     for n in (range(len(A)) if modes is None else modes):
         A[n] = mttkrp(Y, A, n) @ np.linalg.pinv(grams(A).Gamma(n))
     return A
+
+
+# ---------------------------------------------------------------------------
+# HOSVD initialisation (Algorithm 1 step 1; Sec. 4.6: the factors are often
+# initialised with the mode-n singular vectors of the data tensor, then a few
+# ALS sweeps are run)
+# ---------------------------------------------------------------------------
+
+
+def sign_fix(U: np.ndarray) -> np.ndarray:
+    """Sign convention for singular vectors (they are defined up to sign):
+    each column is flipped so that its entry of largest magnitude is positive
+    (the first such entry on ties)."""
+    U = np.array(U, dtype=np.float64, copy=True)
+    for r in range(U.shape[1]):
+        k = int(np.argmax(np.abs(U[:, r])))
+        if U[k, r] < 0:
+            U[:, r] = -U[:, r]
+    return U
+
+
+def hosvd_factors(Y: np.ndarray, R: int) -> List[np.ndarray]:
+    """A^(n) = the R leading left singular vectors of the unfolding Y_(n)
+    (descending singular values, sign_fix applied); needs R <= I_n."""
+    out = []
+    for n in range(Y.ndim):
+        if R > Y.shape[n]:
+            raise ValueError("HOSVD initialisation needs R <= I_n in every mode")
+        U, s, _ = np.linalg.svd(unfold(Y, n), full_matrices=False)
+        out.append(sign_fix(U[:, :R]))
+    return out

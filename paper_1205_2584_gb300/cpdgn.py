@@ -286,6 +286,9 @@ class State:
                                     self.ws.numel(), ctypes.byref(h)), "cp_state_create")
         self._h = h
         self._status_ptr = _lib.cp_state_status(h)
+        # the state's buffer 0 holds the gradient blocks G_n = E_(n) KR_n for
+        # every tensor form except the two-plane one (whose pass gives M_n)
+        self.holds_gradient = shape.y_dtype != CP_BF16X2
         self._host_status = torch.empty(128, dtype=torch.uint8).pin_memory()
 
     def init(self, Y: torch.Tensor, stream=None):

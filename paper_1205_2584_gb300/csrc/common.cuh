@@ -24,6 +24,9 @@ struct Dims {
   int64_t J;                         // prod I_n
   int64_t nfib;                      // J / I_1 (mode-1 fibres)
   int64_t ncore;                     // N R^2
+  int mg;                            // 1: a state's pass writes the gradient blocks
+                                     // G_n = E_(n) KR_n (E = Y - Y_hat) instead of
+                                     // M_n = Y_(n) KR_n (set by cp_state_create)
 };
 
 inline int make_dims(const cp_shape* s, Dims* d) {
@@ -53,6 +56,7 @@ inline int make_dims(const cp_shape* s, Dims* d) {
   d->row0[CP_MAX_N] = d->T;
   d->nfib = d->J / d->I[0];
   d->ncore = int64_t(s->N) * d->RR;
+  d->mg = 0;
   return CP_OK;
 }
 

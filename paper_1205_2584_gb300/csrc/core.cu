@@ -37,6 +37,8 @@ static_assert(kPrepWarps == 4, "the partial sums of k_mode_prep are added as fou
 // CTA (n, j), j < R: column j of Gt^(n), U_n and w_n.
 //   Gt[:, j] = L_G^{-T} L_G^{-1} e_j;  U[:, j] = L_G^{-T} e_j
 //   w_n[:, j] = P^(n) Gt[:, j] - C^(n) (Gamma^(n) Gt[:, j])     (Appendix D)
+//   (P^(n) = A^(n)T M_n; when the state's pass gives the gradient blocks,
+//   P^(n) = A^(n)T G_n and w_n[:, j] = P^(n) Gt[:, j])
 // CTA (n, 0) also writes Gamma^(n,m) for every m.
 // CTA N R + n: L_n = chol(C^(n)) (independent of mu).
 __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double* C, const double* P,
@@ -118,7 +120,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
     const double t = (part[1][0][tid] + part[1][1][tid]) + (part[1][2][tid] + part[1][3][tid]);
     Gt[o] = z[tid];
     U[o] = u[tid];
-    if (w) w[o] = s - t;
+    // with gradient blocks in P (P = A^T G, G = M - A Gamma) the C Gamma term is already in it
+    if (w) w[o] = d.mg ? s : s - t;
   }
 }
 

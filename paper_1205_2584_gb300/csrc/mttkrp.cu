@@ -11,12 +11,18 @@
 //   M_n[i_n] += t_f * prod_{k>=2, k!=n} A^(k)[i_k]   (n >= 2: reuse of t_f, the
 //                                                    partial Khatri-Rao product)
 //   e         = y_f - A^(1) kr_f,  ||E||^2 += e^T e
-// so each tensor element costs 3R multiply-adds whatever N is.  A CTA owns a
+// so each tensor element costs 3R multiply-adds whatever N is.  With `grad`
+// set, e = y - y_hat is formed first and takes the place of y in M_1 and t_f,
+// so the pass gives the gradient blocks G_n = E_(n) KR_n = M_n - A^(n) Gamma^(n)
+// (Sec. 4.6, g = J^T vec(E)) with rounding relative to E rather than to Y.
+// A CTA owns a
 // contiguous range of fibres and keeps its partial M_1 (and M_n, n >= 2, when
 // they fit) in shared memory; partials are added to the float64 outputs at
 // the end.  TA is the arithmetic type: float64 for float64 tensors, float32
 // for float32 and bfloat16 tensors (with float64 accumulation of ||E||^2 per
 // tile and of the cross-CTA sums).
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cpdgn {
@@ -32,6 +38,7 @@ struct MttkrpParams {
   int TF;                // fibres per tile
   int mn_in_smem;        // 1: partial M_n (n >= 2) in shared memory
   int I1p;               // padded leading dimension of the tile
+  int grad;              // 1: accumulate e = y - y_hat instead of y (gradient blocks)
 };
 
 constexpr int kMtThreads = 256;
@@ -133,7 +140,40 @@ __global__ void __launch_bounds__(kMtThreads) k_mttkrp(MttkrpParams p) {
       }
     }
     __syncthreads();
-    // P2: t_f = y_f^T A^(1)  (needed only for M_n, n >= 2)
+    // P3: M_1 rows and the residual; one row per thread.  With p.grad the
+    // tile entry is replaced by e = y - y_hat, which P2 and M_1 then use.
+    for (int i = tid; i < I1; i += kMtThreads) {
+      TA arow[RMAX], acc[RMAX];
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        arow[r] = (r < R) ? A1s[i * R + r] : TA(0);
+        acc[r] = TA(0);
+      }
+      TA e2 = TA(0);
+      for (int f = 0; f < nf; ++f) {
+        const TA y = Yt[f * p.I1p + i];
+        const TA* kf = krs + f * R;
+        TA yh = TA(0);
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) yh = fma(arow[r], kf[r], yh);
+        const TA e = y - yh;
+        e2 = fma(e, e, e2);
+        const TA src = p.grad ? e : y;
+        if (p.grad) Yt[f * p.I1p + i] = e;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) acc[r] = fma(src, kf[r], acc[r]);
+      }
+      e2_total += double(e2);
+      if (want_m) {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) M1s[i * R + r] += acc[r];
+      }
+    }
+    __syncthreads();
+    // P2: t_f = y_f^T A^(1) (or e_f^T A^(1)); needed only for M_n, n >= 2
     if (want_m) {
       for (int e = tid; e < nf * R; e += kMtThreads) {
         const int f = e / R, r = e % R;
@@ -150,38 +190,6 @@ __global__ void __launch_bounds__(kMtThreads) k_mttkrp(MttkrpParams p) {
         ts[f * R + r] = (s0 + s1) + (s2 + s3);
       }
     }
-    // P3: M_1 rows and the residual; one row per thread
-    for (int i = tid; i < I1; i += kMtThreads) {
-      TA arow[RMAX], acc[RMAX];
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r) {
-        arow[r] = (r < R) ? A1s[i * R + r] : TA(0);
-        acc[r] = TA(0);
-      }
-      TA e2 = TA(0);
-      for (int f = 0; f < nf; ++f) {
-        const TA y = Yt[f * p.I1p + i];
-        const TA* kf = krs + f * R;
-        TA yh = TA(0);
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r) {
-          if (r < R) {
-            const TA k = kf[r];
-            acc[r] = fma(y, k, acc[r]);
-            yh = fma(arow[r], k, yh);
-          }
-        }
-        const TA e = y - yh;
-        e2 = fma(e, e, e2);
-      }
-      e2_total += double(e2);
-      if (want_m) {
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-          if (r < R) M1s[i * R + r] += acc[r];
-      }
-    }
-    __syncthreads();
     // P4: M_n, n >= 2, from t_f and the leave-one-out products
     if (want_m) {
       for (int e = tid; e < nf * R; e += kMtThreads) {
@@ -251,6 +259,7 @@ struct Tiled {
   int64_t fib_per_cta;
   int TF, ldy, Rp;                // fibres per tile, tile leading dim, R padded to 4
   int64_t mn_elems;               // sum_{n>=2} I_n R
+  int grad;                       // 1: accumulate e = y - y_hat instead of y
 };
 
 template <typename TY>
@@ -273,16 +282,17 @@ __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ double to_f(double x) { return x; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 
-// Copy nf fibres starting at fibre f0 into the tile buffer (row f at f * ldy).
-template <typename TY>
-__device__ void tile_copy(const TY* Y, int64_t f0, int nf, int I1, int ldy, TY* dst) {
+// Copy nf fibres starting at fibre f0 into the tile buffer (row f at f * ldy);
+// bfloat16 tensors are widened to the float32 tile type TT on the way.
+template <typename TY, typename TT>
+__device__ void tile_copy(const TY* Y, int64_t f0, int nf, int I1, int ldy, TT* dst) {
   const int tot = nf * I1;
   const int64_t base = f0 * I1;
   int f = 0, i = threadIdx.x;
   while (i >= I1 && f < nf) { i -= I1; ++f; }
   for (int e = threadIdx.x; e < tot; e += kT2) {
     if constexpr (sizeof(TY) == 2) {
-      dst[f * ldy + i] = Y[base + e];
+      dst[f * ldy + i] = __bfloat162float(Y[base + e]);
     } else {
       cp_async_elem<TY>(dst + f * ldy + i, Y + base + e);
     }
@@ -291,7 +301,7 @@ __device__ void tile_copy(const TY* Y, int64_t f0, int nf, int I1, int ldy, TY* 
   }
 }
 
-template <typename TY, typename TA, int RMAX, int RPT>
+template <typename TY, typename TT, typename TA, int RMAX, int RPT>
 __global__ void __launch_bounds__(kT2) k_mttkrp_tiled(Tiled p) {
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -307,8 +317,8 @@ __global__ void __launch_bounds__(kT2) k_mttkrp_tiled(Tiled p) {
   TA* ts = krs + size_t(TF) * Rp;                                     // kSeg x TF x Rp partials
   TA* loos = ts + size_t(kSeg) * TF * Rp;                             // (N-1) x TF x Rp
   TA* Mns = loos + size_t(N - 1) * TF * Rp;                           // mn_elems
-  TY* Yt0 = reinterpret_cast<TY*>(Mns + p.mn_elems);                  // 2 x TF x ldy
-  TY* Yt1 = Yt0 + size_t(TF) * ldy;
+  TT* Yt0 = reinterpret_cast<TT*>(Mns + p.mn_elems);                  // 2 x TF x ldy
+  TT* Yt1 = Yt0 + size_t(TF) * ldy;
   int* fidx = reinterpret_cast<int*>(Yt1 + size_t(TF) * ldy + 8);     // TF x CP_MAX_N
   double* red = reinterpret_cast<double*>(
       (reinterpret_cast<uintptr_t>(fidx + TF * CP_MAX_N) + 15) & ~uintptr_t(15));
@@ -337,19 +347,19 @@ __global__ void __launch_bounds__(kT2) k_mttkrp_tiled(Tiled p) {
 
   if (f_begin < f_end) {
     const int nf0 = int((f_end - f_begin) < TF ? (f_end - f_begin) : TF);
-    tile_copy<TY>(Y, f_begin, nf0, I1, ldy, Yt0);
+    tile_copy<TY, TT>(Y, f_begin, nf0, I1, ldy, Yt0);
   }
   cp_async_commit();
   int buf = 0;
   for (int64_t f0 = f_begin; f0 < f_end; f0 += TF) {
     const int nf = int((f_end - f0) < TF ? (f_end - f0) : TF);
-    TY* Ycur = buf ? Yt1 : Yt0;
-    TY* Ynext = buf ? Yt0 : Yt1;
+    TT* Ycur = buf ? Yt1 : Yt0;
+    TT* Ynext = buf ? Yt0 : Yt1;
     // prefetch the next tile
     const int64_t f1 = f0 + TF;
     if (f1 < f_end) {
       const int nf1 = int((f_end - f1) < TF ? (f_end - f1) : TF);
-      tile_copy<TY>(Y, f1, nf1, I1, ldy, Ynext);
+      tile_copy<TY, TT>(Y, f1, nf1, I1, ldy, Ynext);
     }
     cp_async_commit();
     // fibre multi-indices (i_2..i_N) of this tile
@@ -407,19 +417,26 @@ __global__ void __launch_bounds__(kT2) k_mttkrp_tiled(Tiled p) {
 #pragma unroll
           for (int r = 0; r < RMAX; r += 2) {
             if (r < Rp) {     // Rp is a multiple of 4: pairs are whole
-              const TA k0 = kf[r], k1 = kf[r + 1];
-              acc[q][r] = fma(y, k0, acc[q][r]);
-              acc[q][r + 1] = fma(y, k1, acc[q][r + 1]);
-              yh0 = fma(arow[r], k0, yh0);
-              yh1 = fma(arow[r + 1], k1, yh1);
+              yh0 = fma(arow[r], kf[r], yh0);
+              yh1 = fma(arow[r + 1], kf[r + 1], yh1);
             }
           }
           const TA e = y - (yh0 + yh1);
           e2 = fma(e, e, e2);
+          const TA src = p.grad ? e : y;
+          if (p.grad) Ycur[f * ldy + i] = TT(e);
+#pragma unroll
+          for (int r = 0; r < RMAX; r += 2) {
+            if (r < Rp) {
+              acc[q][r] = fma(src, kf[r], acc[q][r]);
+              acc[q][r + 1] = fma(src, kf[r + 1], acc[q][r + 1]);
+            }
+          }
         }
         e2_total += double(e2);
       }
     }
+    if (p.grad) __syncthreads();       // phase A reads rows of other threads
     // phase A: t_f partials over kSeg segments of rows, 4 x 4 blocks
     if (want_m) {
       const int nfb = (nf + 3) / 4, nrb = Rp / 4;
@@ -546,6 +563,7 @@ struct P3 {
   int64_t fib_per_cta;
   int TF, ldy, Rp, ldi, nrb, npairB, FS;
   int mn2_smem;           // 1: mode-2 partial in shared memory
+  int grad;               // 1: accumulate e = y - y_hat instead of y
 };
 
 template <typename TY>
@@ -679,28 +697,8 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
     cp_async_wait<1>();
     __syncthreads();
 
-    // ---- product B: M_1 += Y_tile KR_tile ----
-    if (want_m) {
-#pragma unroll
-      for (int k = 0; k < PB; ++k) {
-        const int q = (tid / FS) + k * (kT3 / FS);
-        const int fs = tid % FS;
-        if (q < p.npairB) {
-          const int rb = q % nrbB, cb = q / nrbB;
-          for (int f = fs; f < nf; f += FS) {
-            const float4 y4 = *reinterpret_cast<const float4*>(Yc + f * ldy + rb * 4);
-            const float4 k4 = *reinterpret_cast<const float4*>(krs + f * Rp + cb * 4);
-            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
-            const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-              for (int v = 0; v < 4; ++v) accB[k][u][v] = fmaf(yv[u], kv[v], accB[k][u][v]);
-          }
-        }
-      }
-    }
-    // ---- product C: residual ----
+    // ---- product C: residual (with p.grad the tile becomes E = Y - Y_hat,
+    // which products B and A then use) ----
     {
       const int nfb = TF / 4;
       float e2 = 0.f;
@@ -727,15 +725,41 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
           if (f < nf) {
             const float4 y4 = *reinterpret_cast<const float4*>(Yc + f * ldy + rb * 4);
             const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+            float ev[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const float e = (rb * 4 + u < I1) ? yv[u] - c[u][v] : 0.f;
+              ev[u] = e;
               e2 = fmaf(e, e, e2);
             }
+            if (p.grad)
+              *reinterpret_cast<float4*>(Yc + f * ldy + rb * 4) = make_float4(ev[0], ev[1], ev[2], ev[3]);
           }
         }
       }
       e2_total += double(e2);
+    }
+    if (p.grad) __syncthreads();
+    // ---- product B: M_1 += Y_tile KR_tile ----
+    if (want_m) {
+#pragma unroll
+      for (int k = 0; k < PB; ++k) {
+        const int q = (tid / FS) + k * (kT3 / FS);
+        const int fs = tid % FS;
+        if (q < p.npairB) {
+          const int rb = q % nrbB, cb = q / nrbB;
+          for (int f = fs; f < nf; f += FS) {
+            const float4 y4 = *reinterpret_cast<const float4*>(Yc + f * ldy + rb * 4);
+            const float4 k4 = *reinterpret_cast<const float4*>(krs + f * Rp + cb * 4);
+            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+            const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) accB[k][u][v] = fmaf(yv[u], kv[v], accB[k][u][v]);
+          }
+        }
+      }
     }
     // ---- product A: t partials ----
     if (want_m) {
@@ -858,7 +882,7 @@ static int launch3_t(const P3& p, int grid, size_t smem, cudaStream_t s) {
 // Returns CP_OK and launches, or CP_EINVAL when the shape does not fit this
 // kernel (the caller then uses the generic pass).
 int launch_mttkrp3(const Dims& d, const void* Y, const double* a, double* m, double* resid2, const int* skip,
-                   cudaStream_t s) {
+                   cudaStream_t s, int grad) {
   if (d.y_dtype == CP_F64) return CP_EINVAL;
   const int I1 = int(d.I[0]);
   const int Rp = (d.R + 3) / 4 * 4;
@@ -916,6 +940,7 @@ int launch_mttkrp3(const Dims& d, const void* Y, const double* a, double* m, dou
   p.npairB = npairB;
   p.FS = FS;
   p.mn2_smem = mn2_smem;
+  p.grad = grad;
   grid = (d.nfib + p.fib_per_cta - 1) / p.fib_per_cta;
   if (d.y_dtype == CP_F32) {
     switch (PB) {
@@ -974,7 +999,8 @@ static size_t mttkrp_smem(const Dims& d, int TF, int I1p, int mn_in_smem, size_t
 
 template <typename TY, typename TA, int RMAX, int RPT>
 static int launch_tiled_t(const Tiled& p, int grid, size_t smem, cudaStream_t s) {
-  auto kern = k_mttkrp_tiled<TY, TA, RMAX, RPT>;
+  using TT = typename std::conditional<sizeof(TY) == 2, float, TY>::type;
+  auto kern = k_mttkrp_tiled<TY, TT, TA, RMAX, RPT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
     return CP_ECUDA;
   kern<<<grid, kT2, smem, s>>>(p);
@@ -1009,14 +1035,19 @@ static size_t tiled_smem(const Dims& d, int TF, int ldy, int Rp, size_t ta, size
 
 // Enqueue one pass (m and resid2 must already be zeroed).
 int launch_mttkrp_tc(const Dims& d, const void* Y, const double* a, double* m, double* resid2, const int* skip,
-                     cudaStream_t s);
+                     cudaStream_t s, int grad);
 
+// grad = 1: the pass gives the gradient blocks E_(n) KR_n instead of M_n
+// (not for the two-plane bfloat16 tensor, whose pass reads Y's planes as
+// tensor-core operands directly: CP_EINVAL there).
 int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, double* resid2,
-                  const int* skip, cudaStream_t s) {
-  if (launch_mttkrp_tc(d, Y, a, m, resid2, skip, s) == CP_OK) return CP_OK;
-  if (launch_mttkrp3(d, Y, a, m, resid2, skip, s) == CP_OK) return CP_OK;
+                  const int* skip, cudaStream_t s, int grad) {
+  if (grad && d.y_dtype == CP_BF16X2) return CP_EINVAL;
+  if (launch_mttkrp_tc(d, Y, a, m, resid2, skip, s, grad) == CP_OK) return CP_OK;
+  if (launch_mttkrp3(d, Y, a, m, resid2, skip, s, grad) == CP_OK) return CP_OK;
   const size_t ta = (d.y_dtype == CP_F64) ? sizeof(double) : sizeof(float);
-  const size_t ty = (d.y_dtype == CP_F64) ? 8 : (d.y_dtype == CP_F32 ? 4 : 2);
+  // shared-memory tile element: bfloat16 tensors are widened to float32
+  const size_t ty = (d.y_dtype == CP_F64) ? 8 : 4;
   const int I1 = int(d.I[0]);
   const size_t max_smem = 220 * 1024;
   if (I1 <= 3 * kT2) {
@@ -1028,11 +1059,7 @@ int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, doub
     TF &= ~3;                                    // phase A works on blocks of 4 fibres
     // leading dimension: odd in 4-byte words (conflict-free strided reads)
     int ldy = I1;
-    if (ty == 4 || ty == 8) {
-      if (ldy % 2 == 0) ldy += 1;              // odd: fibre rows fall in distinct banks
-    } else {
-      ldy += ((2 - ldy % 4) + 4) % 4;          // 2 mod 4 bf16 elements = odd 4-byte words
-    }
+    if (ldy % 2 == 0) ldy += 1;                // odd: fibre rows fall in distinct banks
     size_t smem = tiled_smem(d, TF, ldy, Rp, ta, ty);
     while (smem > max_smem && TF > 4) {
       TF = (TF / 2) & ~3;
@@ -1060,6 +1087,7 @@ int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, doub
       p.ldy = ldy;
       p.Rp = Rp;
       p.mn_elems = int64_t(d.T - d.I[0]) * d.R;
+      p.grad = grad;
       grid = (d.nfib + p.fib_per_cta - 1) / p.fib_per_cta;
       switch (d.y_dtype) {
         case CP_F64: return launch_tiled_q<double, double>(p, int(grid), smem, s);
@@ -1103,6 +1131,7 @@ int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, doub
   p.TF = TF;
   p.mn_in_smem = mn_in_smem;
   p.I1p = I1p;
+  p.grad = grad;
   grid = (d.nfib + p.fib_per_cta - 1) / p.fib_per_cta;
   switch (d.y_dtype) {
     case CP_F64: return launch_r<double, double>(p, int(grid), smem, s);
@@ -1125,7 +1154,7 @@ extern "C" int cp_mttkrp_all(const cp_shape* shape, const void* Y, const double*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CP_CUDA(cudaMemsetAsync(m, 0, size_t(d.T) * d.R * sizeof(double), s));
   if (resid2) CP_CUDA(cudaMemsetAsync(resid2, 0, sizeof(double), s));
-  return launch_mttkrp(d, Y, a, m, resid2, nullptr, s);
+  return launch_mttkrp(d, Y, a, m, resid2, nullptr, s, 0);
 }
 
 namespace cpdgn {
@@ -1143,7 +1172,7 @@ extern "C" int cp_fit(const cp_shape* shape, const void* Y, const double* a, dou
   if (!Y || !a || !resid2) return CP_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CP_CUDA(cudaMemsetAsync(resid2, 0, sizeof(double), s));
-  CP_TRY(launch_mttkrp(d, Y, a, nullptr, resid2, nullptr, s));
+  CP_TRY(launch_mttkrp(d, Y, a, nullptr, resid2, nullptr, s, 0));
   if (rel_err && y_norm2 > 0) {
     k_rel_err<<<1, 32, 0, s>>>(resid2, y_norm2, rel_err);
     if (cudaGetLastError() != cudaSuccess) return CP_ECUDA;

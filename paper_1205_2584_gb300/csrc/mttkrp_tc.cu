@@ -73,6 +73,7 @@ struct TcParams {
   double* m;           // same layout, accumulated; may be null
   double* resid2;      // accumulated; may be null
   const int* skip;
+  int grad;            // 1: the tensor-core products take e = y - y_hat (gradient blocks)
 };
 
 __device__ int g_tc_timeouts = 0;
@@ -428,6 +429,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
         for (int j = 0; j < 32; ++j) {
           const float e = y[j] - ph[j];
           e2 = fmaf(e, e, e2);
+          if (p.grad) y[j] = e;        // the pieces below are then those of E
         }
         racc += double(e2);
 #pragma unroll
@@ -927,6 +929,7 @@ static int launch_tc3(const Dims& d, const void* Y, const double* a, double* m, 
   p.m = m;
   p.resid2 = resid2;
   p.skip = skip;
+  p.grad = 0;
   p3.nplanes = nplanes;
   const int64_t grid = int64_t(p.nc) * p.nb * p.nseg;
   if (grid > (int64_t(1) << 31) - 1) return CP_EINVAL;
@@ -957,10 +960,11 @@ int tc_timeout_counter(int** out) {
 // CP_EINVAL when the shape or pointers do not suit a tensor-core pass (the
 // caller falls back to the SIMT kernels); m and resid2 must be zeroed.
 int launch_mttkrp_tc(const Dims& d, const void* Y, const double* a, double* m, double* resid2, const int* skip,
-                     cudaStream_t s) {
-  if (d.y_dtype == CP_BF16X2) return launch_tc3(d, Y, a, m, resid2, skip, s);   // no other kernel reads it
+                     cudaStream_t s, int grad) {
+  if (d.y_dtype == CP_BF16X2) return grad ? CP_EINVAL : launch_tc3(d, Y, a, m, resid2, skip, s);
   if (tc_disabled()) return CP_EINVAL;
-  if (d.y_dtype == CP_BF16) return launch_tc3(d, Y, a, m, resid2, skip, s);
+  // the bfloat16 pass feeds Y's plane to the MMAs directly: no gradient form
+  if (d.y_dtype == CP_BF16) return grad ? CP_EINVAL : launch_tc3(d, Y, a, m, resid2, skip, s);
   if (d.N != 3 || d.y_dtype != CP_F32 || d.R > 32 || d.R < 1) return CP_EINVAL;
   if (d.I[0] % 4 != 0 || (reinterpret_cast<uintptr_t>(Y) & 15) != 0) return CP_EINVAL;
   if (d.I[0] > (int64_t(1) << 30) || d.I[1] > (int64_t(1) << 30) || d.I[2] > (int64_t(1) << 30)) return CP_EINVAL;
@@ -989,6 +993,7 @@ int launch_mttkrp_tc(const Dims& d, const void* Y, const double* a, double* m, d
   p.m = m;
   p.resid2 = resid2;
   p.skip = skip;
+  p.grad = grad;
   const int64_t grid = int64_t(p.nc) * p.nb * p.nseg;
   if (grid > (int64_t(1) << 31) - 1) return CP_EINVAL;
   return launch_tc(tm, p, int(grid), s);

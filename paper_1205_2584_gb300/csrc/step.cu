@@ -28,7 +28,7 @@
 namespace cpdgn {
 
 int launch_mttkrp(const Dims& d, const void* Y, const double* a, double* m, double* resid2,
-                  const int* skip, cudaStream_t s);
+                  const int* skip, cudaStream_t s, int grad);
 int launch_gram(const Dims& d, const double* a, const double* m, double* part, double* C, double* P,
                 double* Gnm, double* Gall, const int* skip, cudaStream_t s);
 int launch_mode_prep(const Dims& d, const double* C, const double* P, const double* mu, double* Gnm,
@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(kUpdRows * 32) k_update(Dims d, const double* 
       s1 = fma(Arow[row][s], Gam[s + R * r], s1);
       s2 = fma(Arow[row][s], Fn[s + R * r], s2);
     }
-    g = Mn[i + In * r] - s1;          // gradient block G_n = M_n - A^(n) Gamma^(n)
+    // gradient block G_n = M_n - A^(n) Gamma^(n), or G_n itself from the pass
+    g = d.mg ? Mn[i + In * r] : Mn[i + In * r] - s1;
     H[row][r] = g - s2;               // G_n - A^(n) F_n
   }
   __syncthreads();
@@ -584,6 +585,10 @@ extern "C" int cp_state_create(const cp_shape* shape, const cp_opts* opts, doubl
   if (ws_bytes < L.total) return CP_ENOMEM;
   cp_state* st = new (std::nothrow) cp_state;
   if (!st) return CP_ENOMEM;
+  // the pass gives the gradient blocks directly (from the residual tensor,
+  // accurate relative to the gradient rather than to the MTTKRP) wherever
+  // the kernel for the shape can; the two-plane tensor-core pass gives M_n
+  d.mg = (d.y_dtype == CP_BF16X2) ? 0 : 1;
   st->d = d;
   st->o = *opts;
   st->a = a;
@@ -698,7 +703,7 @@ extern "C" int cp_als_sweep(cp_state* st, const void* Y, int sweeps, void* strea
   for (int it = 0; it < sweeps; ++it)
     for (int n = 0; n < d.N; ++n) {
       CP_CUDA(cudaMemsetAsync(B.m, 0, size_t(d.T) * d.R * sizeof(double), s));
-      CP_TRY(launch_mttkrp(d, Y, st->a, B.m, nullptr, nullptr, s));
+      CP_TRY(launch_mttkrp(d, Y, st->a, B.m, nullptr, nullptr, s, 0));
       CP_TRY(launch_gram(d, st->a, nullptr, B.gpart, B.C, nullptr, B.Gnm, nullptr, nullptr, s));
       int64_t g = (d.I[n] + kAlsThreads - 1) / kAlsThreads;
       if (g > 4 * kSMs) g = 4 * kSMs;
@@ -729,7 +734,7 @@ extern "C" int cp_state_init(cp_state* st, const void* Y, void* stream) {
   CP_CUDA(cudaMemsetAsync(B.m, 0, size_t(d.T) * d.R * sizeof(double), s));
   CP_CUDA(cudaMemsetAsync(B.scal, 0, 64 * sizeof(double), s));
   CP_CUDA(cudaMemsetAsync(B.info, 0, 64 * sizeof(int), s));
-  CP_TRY(launch_mttkrp(d, Y, st->a, B.m, B.scal + SC_R2, nullptr, s));
+  CP_TRY(launch_mttkrp(d, Y, st->a, B.m, B.scal + SC_R2, nullptr, s, d.mg));
   int64_t g = (d.J + 255) / 256;
   if (g > 4 * kSMs) g = 4 * kSMs;
   k_sumsq<<<unsigned(g), 256, 0, s>>>(Y, d.y_dtype, d.J, B.scal + SC_YN2);
@@ -775,7 +780,7 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
   const int64_t nupd = update_ctas(d);
   k_update<<<unsigned(nupd), kUpdRows * 32, 0, s>>>(d, st->a, B.m, B.Gnm, B.Gt, B.f, mu, B.delta, B.at,
                                                     B.part, skip);
-  CP_TRY(launch_mttkrp(d, Y, B.at, B.mt, B.scal + SC_R2T, skip, s));
+  CP_TRY(launch_mttkrp(d, Y, B.at, B.mt, B.scal + SC_R2T, skip, s, d.mg));
   k_control<<<1, 256, 0, s>>>(d, st->o, B.part, nupd, B.status, B.scal, B.info, B.scale, st->tmo);
   int64_t gc = (nm + 255) / 256;
   if (gc > 4 * kSMs) gc = 4 * kSMs;

@@ -5,9 +5,9 @@
     the same rule on the same tensor values: the float64 form within 1e-10
     of the oracle's final epsilon, the reduced-precision forms within 1e-6.
   * One mixed step on the large served class (400^3, R = 30, core
-    N R^2 = 2700): the pass's MTTKRP on sampled rows, the float64 algebra of
-    the step against the oracle's fLM_a step from the GPU's own MTTKRP, and
-    the trial residual.
+    N R^2 = 2700): the pass's gradient blocks on sampled rows, the float64
+    algebra of the step against the oracle's fLM_a step from the GPU's own
+    pass output, and the trial residual.
   * One step from a collinear state near convergence where mu is small and
     the core is ill-conditioned (kappa(core) ~ 4e5 and ~ 1e7): the mixed
     solve against the float64 solve within max(1e-10, 1e-15 kappa), and the
@@ -101,7 +101,10 @@ def test_large_core_mixed_step_400cubed(cp, record_property):
     st.init(Y)
     torch.cuda.synchronize()
     nA = p.R * sum(p.dims)
-    M_gpu = [x.numpy().copy() for x in cp.split_factors(st.buffer(cp.State.BUF_M, nA).cpu(), p.dims, p.R)]
+    G_gpu = [x.numpy().copy() for x in cp.split_factors(st.buffer(cp.State.BUF_M, nA).cpu(), p.dims, p.R)]
+    assert st.holds_gradient                 # float32 tensor: the pass gives G_n = E_(n) KR_n
+    g0 = O.grams(p.init)
+    M_gpu = [b + x @ g0.Gamma(n) for n, (x, b) in enumerate(zip(p.init, G_gpu))]
     st.step(Y)
     torch.cuda.synchronize()
     s = st.status()
@@ -109,13 +112,15 @@ def test_large_core_mixed_step_400cubed(cp, record_property):
     st.close()
     del Y
     rng = np.random.default_rng(5)
+    E = p.Y - O.cp_full(p.init)
     for n in range(3):
         KR = O.kr_except(p.init, n)
-        Yn = O.unfold(p.Y, n)
+        En = O.unfold(E, n)
         for i in rng.integers(0, p.dims[n], size=3):
-            ref = Yn[i] @ KR
-            assert rel([M_gpu[n][i]], [ref]) < 2e-5, (n, i)
-        del KR, Yn
+            ref = En[i] @ KR                 # row i of the gradient block, one by one
+            assert rel([G_gpu[n][i]], [ref]) < 2e-5, (n, i)
+        del KR, En
+    del E
     own = O.flm_step(p.Y, p.init, mu, M=M_gpu)
     err = rel(delta, own.delta)
     record_property("step_rel_err_vs_oracle_same_M", err)

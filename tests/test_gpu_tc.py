@@ -88,7 +88,9 @@ def test_tc_lm_run_reaches_oracle_fit(cp, core_mode):
 def _one_step_check(cp, dtype, mu, record=None):
     """One fLM step on a reduced-precision tensor against the oracle on the
     same stored values, split into its two error sources:
-      (1) the pass: the GPU's MTTKRP M against the oracle's (float32-level);
+      (1) the pass: the GPU's MTTKRP M against the oracle's (float32-level),
+          and, where the pass gives the gradient blocks G_n = E_(n) KR_n
+          directly (float32 tensors), G against the oracle's M - A Gamma;
       (2) the float64 algebra: the GPU step against the oracle's fLM_a step
           computed from the GPU's own M, held to max(1e-10, 1e-15 kappa(core));
       (3) end to end: the GPU step against the oracle's own step, bounded by
@@ -105,7 +107,16 @@ def _one_step_check(cp, dtype, mu, record=None):
     st.init(Y)
     torch.cuda.synchronize()
     nA = p.R * sum(p.dims)
-    M_gpu = [x.numpy().copy() for x in cp.split_factors(st.buffer(cp.State.BUF_M, nA).cpu(), p.dims, p.R)]
+    B_gpu = [x.numpy().copy() for x in cp.split_factors(st.buffer(cp.State.BUF_M, nA).cpu(), p.dims, p.R)]
+    g0 = O.grams(p.init)
+    if st.holds_gradient:
+        # the pass gave the gradient blocks G_n = E_(n) KR_n; M_n = G_n + A^(n) Gamma^(n)
+        G_ref = O.gradient_blocks(p.Y, p.init)
+        for n in range(3):
+            assert rel(B_gpu[n], G_ref[n]) < 2e-5, n
+        M_gpu = [b + a @ g0.Gamma(n) for n, (a, b) in enumerate(zip(p.init, B_gpu))]
+    else:
+        M_gpu = B_gpu
     st.step(Y)
     torch.cuda.synchronize()
     delta = [x.numpy() for x in cp.split_factors(st.buffer(cp.State.BUF_DELTA, nA).cpu(), p.dims, p.R)]

@@ -554,3 +554,46 @@ def test_als_exact_factors_are_a_fixed_point():
     p = synth.make_problem(33, (6, 5, 7), 3, snr_db=None)
     A = O.als_sweep(p.Y, p.true_factors)
     assert _rel(A, p.true_factors) < 1e-11
+
+
+# ------------------------------------------------------------------ HOSVD
+
+
+def test_hosvd_matches_eigenvectors_of_the_unfolding_gram():
+    """The oracle's HOSVD (an SVD of Y_(n)) against an independent route: the
+    leading eigenvectors of Y_(n) Y_(n)^T by a symmetric eigensolver, compared
+    as subspace projectors and, with the sign convention applied, column by
+    column (the singular values are distinct here)."""
+    p = synth.make_problem(50, (9, 10, 11), 3, snr_db=20)
+    U = O.hosvd_factors(p.Y, 3)
+    for n in range(3):
+        Yn = O.unfold(p.Y, n)
+        w, V = np.linalg.eigh(Yn @ Yn.T)
+        V = O.sign_fix(V[:, ::-1][:, :3])
+        assert np.allclose(U[n] @ U[n].T, V @ V.T, atol=1e-10)
+        assert np.allclose(U[n], V, atol=1e-9)
+        assert np.allclose(U[n].T @ U[n], np.eye(3), atol=1e-12)
+
+
+def test_hosvd_recovers_orthogonal_factor_subspaces():
+    """A noiseless CP tensor with orthonormal factor columns and distinct
+    weights: the mode-n singular vectors are the factor columns (up to
+    order and sign), so the HOSVD subspace is the factor's column space."""
+    rng = np.random.default_rng(51)
+    dims, R = (7, 8, 9), 3
+    Q = [np.linalg.qr(rng.standard_normal((I, R)))[0] for I in dims]
+    lam = np.array([5.0, 3.0, 1.5])
+    Y = O.cp_full([Q[0] * lam[None, :], Q[1], Q[2]])
+    U = O.hosvd_factors(Y, R)
+    for n in range(3):
+        assert np.allclose(U[n] @ U[n].T, Q[n] @ Q[n].T, atol=1e-12)
+        # singular values of Y_(n) are the weights: columns in weight order, up to sign
+        assert np.allclose(np.abs(U[n].T @ Q[n]), np.eye(R), atol=1e-12)
+
+
+def test_sign_fix_convention():
+    U = np.array([[0.1, -0.9], [-0.8, 0.2], [0.3, 0.1]])
+    V = O.sign_fix(U)
+    assert np.array_equal(V[:, 0], -U[:, 0]) and np.array_equal(V[:, 1], -U[:, 1])
+    with pytest.raises(ValueError):
+        O.hosvd_factors(np.zeros((2, 3, 4)), 3)
