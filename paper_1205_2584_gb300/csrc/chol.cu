@@ -98,37 +98,104 @@ __device__ bool grid_barrier(CholSync* sy, unsigned G, unsigned& epoch, int* inf
   return s_ok != 0;
 }
 
-// Factor the kb x kb tile D (lower part) in place; warp 0 only, lane = row.
-// rinv[j] = 1 / L_jj.  Returns (lane 0) the first bad pivot, 1-based, or 0.
+// 1 / d for d > 0 (finite) by Newton's iteration for the reciprocal,
+// x <- x (2 - d x), written as x + x (1 - d x), from the hardware's
+// approximate double reciprocal: two iterations take its ~2^-20 relative
+// error below the rounding of a double, in four dependent multiply-adds.
+__device__ __forceinline__ double recip64(double d) {
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+  x = fma(x, fma(-d, x, 1.0), x);
+  x = fma(x, fma(-d, x, 1.0), x);
+  return x;
+}
+
+// Factor the kb x kb tile D (lower part) in place with the whole CTA.
+// Column j of the elimination needs only the reciprocal of its pivot:
+// D[i][k] -= D[i][j] D[k][j] / D[j][j] for j < k <= i, with column j itself
+// left unscaled; the square roots L_jj = sqrt(d_j), L_ij = D[i][j] / sqrt(d_j)
+// and rinv[j] = 1 / L_jj are formed at the end for all columns at once.
+//
+// On this part every float64 warp instruction holds the SM's float64 units
+// for about 16 clocks, so the work of a column is packed into as few warps as
+// possible: the packed lower-triangle entries are numbered column by column
+// from the last column down (k = 31 first), so the entries still to update
+// at column j (k > j) are a prefix of the numbering and the warps beyond it
+// skip the column.  The reciprocal of the next pivot is formed once, by the
+// thread that updates that pivot, and shared through shared memory.
+// Thread t owns entries t, t + CT, t + 2 CT.  Returns the first bad pivot
+// (1-based) or 0; every thread gets it.
 __device__ int factor_tile(double (*D)[CB + 1], int kb, double* rinv) {
-  const int lane = threadIdx.x & 31;
-  double a[CB];
+  constexpr int NE = CB * (CB + 1) / 2;           // 528 packed entries
+  constexpr int PER = (NE + CT - 1) / CT;         // 3
+  __shared__ double s_q[CB];
+  __shared__ int s_fbad;
+  int ei[PER], ek[PER];
 #pragma unroll
-  for (int j = 0; j < CB; ++j)
-    a[j] = (lane < kb && j < kb) ? (j <= lane ? D[lane][j] : 0.0) : (lane == j ? 1.0 : 0.0);
-  int bad = 0;
-#pragma unroll
-  for (int j = 0; j < CB; ++j) {
-    double piv = __shfl_sync(0xffffffffu, a[j], j);
-    if (!(piv > 0.0) || !isfinite(piv)) {
-      if (bad == 0 && j < kb) bad = j + 1;
-      piv = 1.0;
-      if (lane == j) a[j] = 1.0;
+  for (int q = 0; q < PER; ++q) {
+    int e = int(threadIdx.x) + q * CT, i = -1, k = -1;
+    if (e < NE) {                                  // column k holds 32 - k entries
+      k = CB - 1;
+      while (e >= CB - k) { e -= CB - k; --k; }
+      i = k + e;
     }
-    const double r = rsqrt(piv);                 // every lane: 1 / L_jj
-    const double lij = a[j] * r;                 // lane > j: L_ij; lane j: L_jj
-    a[j] = lij;
-    if (lane == 0) rinv[j] = r;
+    ei[q] = i;
+    ek[q] = k;
+  }
+  // rows / columns beyond kb: identity, so the padded tile factors trivially
 #pragma unroll
-    for (int l = j + 1; l < CB; ++l) {
-      const double llj = __shfl_sync(0xffffffffu, lij, l);
-      if (l <= lane) a[l] = fma(-lij, llj, a[l]);
+  for (int q = 0; q < PER; ++q)
+    if (ei[q] >= kb) D[ei[q]][ek[q]] = (ei[q] == ek[q]) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) s_fbad = 0;
+  __syncthreads();
+  // reciprocal of pivot 0 (an invalid pivot is recorded and replaced by 1)
+  if (threadIdx.x == 0) {
+    double d = D[0][0];
+    if (!(d > 0.0) || !isfinite(d)) {
+      s_fbad = 1;
+      d = 1.0;
+    }
+    s_q[0] = recip64(d);
+  }
+  __syncthreads();
+  for (int j = 0; j < CB - 1; ++j) {
+    const double qj = s_q[j];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = ei[q], k = ek[q];
+      if (k > j) {
+        const double v = fma(-D[i][j] * qj, D[k][j], D[i][k]);
+        D[i][k] = v;
+        if (i == j + 1 && k == j + 1) {            // the next pivot: its reciprocal now
+          double d = v;
+          if (!(d > 0.0) || !isfinite(d)) {
+            if (s_fbad == 0) s_fbad = j + 2;
+            d = 1.0;
+          }
+          s_q[j + 1] = recip64(d);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // square roots of the pivots, then the columns
+  if (threadIdx.x < CB) {
+    double d = D[threadIdx.x][threadIdx.x];
+    if (!(d > 0.0) || !isfinite(d)) d = 1.0;
+    rinv[threadIdx.x] = rsqrt(d);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = ei[q], k = ek[q];
+    if (i >= 0) {
+      const double v = D[i][k];
+      D[i][k] = (i == k) ? ((v > 0.0 && isfinite(v)) ? v * rinv[k] : 1.0) : v * rinv[k];
     }
   }
-#pragma unroll
-  for (int j = 0; j < CB; ++j)
-    if (j <= lane) D[lane][j] = a[j];
-  return bad;
+  __syncthreads();
+  const int bad = s_fbad;
+  return (bad > 0 && bad <= kb) ? bad : 0;
 }
 
 __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* dinv, int* info, CholSync* sy,
@@ -151,9 +218,9 @@ __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* din
       D[i][j] = (i < kb && j <= i) ? A[(k0 + i) + n * (k0 + j)] : 0.0;
     }
     __syncthreads();
-    if (warp == 0) {
+    {
       const int bad = factor_tile(D, kb, rinv);
-      if (lane == 0) s_bad = bad;
+      if (tid == 0) s_bad = bad;
     }
     __syncthreads();
     for (int64_t r = k0 + kb + int64_t(cta) * 8 + warp; r < n; r += int64_t(G) * 8) {
@@ -174,6 +241,8 @@ __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* din
         const int i = e % kb, j = e / kb;
         if (j <= i) A[(k0 + i) + n * (k0 + j)] = D[i][j];
       }
+      // 1 / L_jj: the diagonal of L_kk^{-1}, read by the inverse phase below
+      if (tid < CB) dinv[int64_t(k) * CB * CB + tid * (CB + 1)] = rinv[tid];
     }
     if (k + 1 == nb) break;
     // ---- phase B: trailing update of the lower triangle ----
@@ -226,14 +295,17 @@ __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* din
       }
       __syncwarp();
       double* Xc = dinv + int64_t(c) * CB * CB;
+      const double ri = (lane < cb) ? Xc[lane * (CB + 1)] : 1.0;     // 1 / L_ii, lane i
+      __syncwarp();
       // lane j: column j of L^{-1} by forward substitution, x_i = 0 for i < j
       double x[CB];
 #pragma unroll
       for (int i = 0; i < CB; ++i) {
+        const double rii = __shfl_sync(0xffffffffu, ri, i);
         if (i < lane) {
           x[i] = 0.0;
         } else if (i == lane) {
-          x[i] = 1.0 / Lt[i][i];
+          x[i] = rii;
         } else {
           double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
@@ -243,7 +315,7 @@ __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* din
             if (l + 2 < i) s2 = fma(Lt[i][l + 2], x[l + 2], s2);
             if (l + 3 < i) s3 = fma(Lt[i][l + 3], x[l + 3], s3);
           }
-          x[i] = -((s0 + s1) + (s2 + s3)) / Lt[i][i];
+          x[i] = -((s0 + s1) + (s2 + s3)) * rii;
         }
       }
 #pragma unroll
@@ -262,6 +334,7 @@ __global__ void __launch_bounds__(CT) k_trsv64(const double* L, const double* di
   __shared__ int s_c;
   __shared__ double part[8][CB];
   __shared__ double rr[CB];
+  __shared__ double Xs[CB][CB + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nb = int((n + CB - 1) / CB);
   if (tid == 0) s_c = atomicAdd(&sy->ticket, 1);
@@ -271,45 +344,56 @@ __global__ void __launch_bounds__(CT) k_trsv64(const double* L, const double* di
   const int c = backward ? nb - 1 - t : t;
   const int64_t c0 = int64_t(c) * CB;
   const int cb = int((n - c0) < CB ? (n - c0) : CB);
+  // the diagonal tile's inverse and the right-hand side do not depend on
+  // any other block: fetch them before the first wait
+  {
+    const double* Xc = dinv + int64_t(c) * CB * CB;
+    for (int e = tid; e < CB * CB; e += CT) Xs[e % CB][e / CB] = Xc[e];
+  }
+  const double bl = (tid < cb) ? b[c0 + tid] : 0.0;
   double acc = 0.0;                // forward: row c0 + lane; backward: outputs 4 warp .. 4 warp + 3
   double accb[4] = {0.0, 0.0, 0.0, 0.0};
   bool ok = true;
   const int j_lo = backward ? c + 1 : 0, j_hi = backward ? nb : c;
   for (int jj = j_lo; jj < j_hi && ok; ++jj) {
     const int j = backward ? (nb - 1 - (jj - j_lo)) : jj;     // wait in publication order
+    const int64_t j0 = int64_t(j) * CB;
+    const int jb = int((n - j0) < CB ? (n - j0) : CB);
+    // this thread's entries of the off-diagonal tile, loaded before the wait
+    double lv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int l = 4 * warp + q;
+      if (!backward) lv[q] = (l < jb && lane < cb) ? L[(c0 + lane) + n * (j0 + l)] : 0.0;
+      else lv[q] = (l < cb && lane < jb) ? L[(j0 + lane) + n * (c0 + l)] : 0.0;
+    }
     if (lane == 0) {
       const uint64_t t0 = chol_gtimer();
-      for (;;) {
+      for (int it = 0;; ++it) {
         if (*reinterpret_cast<volatile int*>(&sy->flags[j])) break;
         if (*reinterpret_cast<volatile int*>(&sy->abort)) { ok = false; break; }
-        if (chol_gtimer() - t0 > kWaitNs) {
+        if ((it & 63) == 63 && chol_gtimer() - t0 > kWaitNs) {
           chol_fail(sy, info, n, tmo);
           ok = false;
           break;
         }
-        __nanosleep(32);
       }
     }
     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
     if (!ok) break;
     __threadfence();
-    const int64_t j0 = int64_t(j) * CB;
-    const int jb = int((n - j0) < CB ? (n - j0) : CB);
     if (!backward) {
       // acc(row c0 + lane) += sum over this warp's 4 columns l of L[c0 + lane, j0 + l] x[j0 + l]
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int l = 4 * warp + q;
-        if (l < jb && lane < cb) acc = fma(L[(c0 + lane) + n * (j0 + l)], __ldcg(x + j0 + l), acc);
+        if (l < jb) acc = fma(lv[q], __ldcg(x + j0 + l), acc);
       }
     } else {
       // output i = 4 warp + q: sum over rows l (= lane) of L[j0 + l, c0 + i] x[j0 + l]
       const double xl = lane < jb ? __ldcg(x + j0 + lane) : 0.0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = 4 * warp + q;
-        if (i < cb && lane < jb) accb[q] = fma(L[(j0 + lane) + n * (c0 + i)], xl, accb[q]);
-      }
+      for (int q = 0; q < 4; ++q) accb[q] = fma(lv[q], xl, accb[q]);
     }
   }
   if (!backward) {
@@ -326,39 +410,35 @@ __global__ void __launch_bounds__(CT) k_trsv64(const double* L, const double* di
   __syncthreads();
   if (*reinterpret_cast<volatile int*>(&sy->abort)) return;
   if (tid < CB) {
-    double s = 0.0;
+    double sum = 0.0;
     if (!backward) {
-      for (int w = 0; w < 8; ++w) s += part[w][tid];
+      for (int w = 0; w < 8; ++w) sum += part[w][tid];
     } else {
-      s = part[0][tid];
+      sum = part[0][tid];
     }
-    rr[tid] = tid < cb ? b[c0 + tid] - s : 0.0;
+    rr[tid] = tid < cb ? bl - sum : 0.0;
   }
   __syncthreads();
   if (tid < CB) {
-    const double* Xc = dinv + int64_t(c) * CB * CB;
     double s0 = 0.0, s1 = 0.0;
     if (!backward) {
 #pragma unroll 8
       for (int l = 0; l < CB; l += 2) {
-        s0 = fma(Xc[tid + CB * l], rr[l], s0);
-        s1 = fma(Xc[tid + CB * (l + 1)], rr[l + 1], s1);
+        s0 = fma(Xs[tid][l], rr[l], s0);
+        s1 = fma(Xs[tid][l + 1], rr[l + 1], s1);
       }
     } else {
 #pragma unroll 8
       for (int l = 0; l < CB; l += 2) {
-        s0 = fma(Xc[l + CB * tid], rr[l], s0);
-        s1 = fma(Xc[(l + 1) + CB * tid], rr[l + 1], s1);
+        s0 = fma(Xs[l][tid], rr[l], s0);
+        s1 = fma(Xs[l + 1][tid], rr[l + 1], s1);
       }
     }
     if (tid < cb) x[c0 + tid] = s0 + s1;
     __threadfence();
   }
   __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    atomicExch(&sy->flags[c], 1);
-  }
+  if (tid == 0) atomicExch(&sy->flags[c], 1);
 }
 
 static int chol64_grid() {
