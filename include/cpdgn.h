@@ -75,9 +75,10 @@ enum cp_code {
 enum cp_core_mode {
   CP_CORE_F64 = 0,    /* float64 Cholesky of the core system */
   CP_CORE_MIXED = 1   /* float32 Gauss-Jordan inverse + float64 iterative refinement;
-                         a trial whose refinement does not reach 1e-14 ||b|| (an
-                         ill-conditioned core) is solved by the float64 Cholesky
-                         instead (cp_status.core_f64 = 1) */
+                         a trial whose refinement does not reach 1e-14 ||b|| for a
+                         float64 tensor, 1e-8 ||b|| for a float32 / bfloat16 one
+                         (an ill-conditioned core) is solved by the float64
+                         Cholesky instead (cp_status.core_f64 = 1) */
 };
 
 /* stop reasons in cp_status.stop */
@@ -135,8 +136,8 @@ typedef struct cp_status {
   int32_t refine_sweeps;   /* refinement residuals formed by the last CP_CORE_MIXED solve */
   int32_t core_f64;        /* 1 if the last CP_CORE_MIXED trial solved its core system
                               by the float64 Cholesky fallback (the refinement did
-                              not reach 1e-14 ||b||, or the float32 inverse met a
-                              bad pivot); 0 otherwise */
+                              not reach its target, see CP_CORE_MIXED, or the
+                              float32 inverse met a bad pivot); 0 otherwise */
 } cp_status;
 
 typedef struct cp_state cp_state;   /* opaque host handle */
@@ -344,6 +345,68 @@ int cp_als_sweep(cp_state* st, const void* Y, int sweeps, void* stream);
  * 2 = Gt (N R x R), 3 = w (N R^2), 4 = f (N R^2), 5 = a_trial (R*T).
  * Returns NULL for an unknown id. */
 double* cp_state_buffer(cp_state* st, int id);
+
+/* ---- HOSVD initialisation (Algorithm 1 step 1; Sec. 4.6) ---- */
+
+/* Bytes of device workspace cp_hosvd needs for this shape (host-only). */
+int cp_hosvd_workspace_bytes(const cp_shape* shape, size_t* bytes);
+
+/* Initial factors from the mode-n singular vectors of the data tensor (the
+ * initialisation Sec. 4.6 describes, followed there by a few ALS sweeps, see
+ * cp_als_sweep):  A^(n) <- the R leading left singular vectors of the
+ * unfolding Y_(n), i.e. the R leading eigenvectors of Y_(n) Y_(n)^T, in
+ * descending order, each column's sign fixed so that its entry of largest
+ * magnitude is positive.  Y: the tensor in shape->y_dtype; a: the float64
+ * factor vector (Eq. vecV), overwritten; ws: cp_hosvd_workspace_bytes(shape)
+ * bytes.  Y_(n) Y_(n)^T is accumulated in float64 on the device; its leading
+ * eigenvectors come from `iters` steps of subspace iteration with
+ * m = R + min(R, 32) (at most I_n) columns orthonormalised by Cholesky QR,
+ * then a Rayleigh-Ritz step with a Jacobi eigensolver; the result converges
+ * like (lambda_{m+1} / lambda_R)^iters.  Needs R <= I_n in every mode
+ * (else CP_EINVAL), 1 <= iters <= 1000; asynchronous on `stream`. */
+int cp_hosvd(const cp_shape* shape, const void* Y, double* a, int iters, void* ws, size_t ws_bytes,
+             void* stream);
+
+/* ---- the damped Hessian's inverse in block form (Theorem 4) and MedSAE ---- */
+
+/* Bytes of device workspace cp_hinv_blocks needs (host-only). */
+int cp_hinv_workspace_bytes(const cp_shape* shape, size_t* bytes);
+
+/* Theorem 4's memory-saving form of (H + mu I)^{-1}, H = J^T J at the factors
+ * `a` (Eq. vecV) and damping *mu (device scalar):
+ *   block (n, m) = delta_nm (Gt^(n) kron I_{I_n})
+ *                  - (I_R kron A^(n)) St^(n,m) (I_R kron A^(m)T)            (Eq. fastblock)
+ *   Gt^(n) = (Gamma^(n) + mu I)^{-1}  -> Gt: N R x R (column-major, back to back);
+ *   St = D B_mu D, D = blkdiag(Gt^(n) kron I_R), B_mu = K (I + Psi_mu K)^{-1}
+ *   (Eq. inverse_f1a)                 -> St: N R^2 x N R^2 column-major, block
+ *   (n, m) = St^(n,m) (rows n R^2 .., columns m R^2 ..), symmetric.
+ * B_mu is formed as K - K S M^{-1} S^T K with the symmetric positive definite
+ * core M = I + S^T K S factored by the float64 Cholesky (cp_dgn_solve).
+ * The two outputs hold N R^2 + N^2 R^4 numbers against the (R T)^2 of the
+ * inverse itself.  info (device int): 0, or a failed pivot as in
+ * cp_dgn_core_build / cp_dgn_solve (the outputs are then not valid).  ws:
+ * cp_hinv_workspace_bytes(shape) bytes.  Float64 throughout; O((N R^2)^3)
+ * operations; N R^2 <= 6400.  Asynchronous on `stream`. */
+int cp_hinv_blocks(const cp_shape* shape, const double* a, const double* mu, double* Gt, double* St,
+                   int* info, void* ws, size_t ws_bytes, void* stream);
+
+/* The diagonal of (H + mu I)^{-1} (R T values in the order of Eq. vecV) from
+ * Theorem 4's blocks: entry (A^(n)[i, r]) =
+ *   Gt^(n)[r, r] - sum_{s, s'} A^(n)[i, s] St^(n,n)[s + R r, s' + R r] A^(n)[i, s'].
+ * Gt, St as written by cp_hinv_blocks for the same `a`. */
+int cp_hinv_diag(const cp_shape* shape, const double* a, const double* Gt, const double* St, double* diag,
+                 void* stream);
+
+/* Squared angular errors between true and estimated components (Sec. 6,
+ * Eq. MedSAE), after matching the components' order: the permutation pi
+ * maximises sum_r sum_n |cos(a_r^(n), ahat_pi(r)^(n))| (solved exactly by the
+ * Hungarian method), and alpha2[n R + r] = arccos(|cos(a_r^(n), ahat_pi(r)^(n))|)^2
+ * (the absolute value: a component's sign is fixed only up to flips that
+ * cancel across modes); perm[r] = pi(r).  a_true, a_est: factor vectors of
+ * the same shape (Eq. vecV); alpha2: N R doubles; perm: R ints (device).
+ * MedSAE in dB is 10 log10 of the median of alpha2 over the runs compared. */
+int cp_sae(const cp_shape* shape, const double* a_true, const double* a_est, double* alpha2, int* perm,
+           void* stream);
 
 /* ---- batched form: many small decompositions in one persistent launch ---- */
 

@@ -527,3 +527,93 @@ def hosvd_factors(Y: np.ndarray, R: int) -> List[np.ndarray]:
         U, s, _ = np.linalg.svd(unfold(Y, n), full_matrices=False)
         out.append(sign_fix(U[:, :R]))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Theorem 4: the damped Hessian's inverse in block form (memory saving), and
+# the MedSAE measure of Sec. 6 (Eq. MedSAE)
+# ---------------------------------------------------------------------------
+
+
+def hinv_blocks(A, mu: float):
+    """Theorem 4's compact representation of H_mu^{-1}: Gt^(n) (N matrices
+    R x R) and St = D B_mu D (N R^2 x N R^2), D = blkdiag(Gt^(n) kron I_R),
+    B_mu = K (I + Psi_mu K)^{-1} (Eq. inverse_f1a); block (n, m) of St is
+    St^(n,m).  Reading: the proof's B^(n,m) is the (n, m) block of B_mu (the
+    block the product L_mu B_mu L_mu^T places at (n, m))."""
+    g = grams(A)
+    N, R = len(A), A[0].shape[1]
+    Gt = damped_inverses(g, mu)
+    K = kernel_K(g)
+    Psi = psi_mu(g, Gt)
+    n = N * R * R
+    B = K @ np.linalg.inv(np.eye(n) + Psi @ K)
+    D = sla.block_diag(*[np.kron(Gt[k], np.eye(R)) for k in range(N)])
+    return Gt, D @ B @ D
+
+
+def hinv_from_blocks(A, Gt, St) -> np.ndarray:
+    """Eq. fastblock: H_mu^{-1} block (n, m) =
+    delta_nm (Gt^(n) kron I_{I_n}) - (I_R kron A^(n)) St^(n,m) (I_R kron A^(m)T)."""
+    N, R = len(A), A[0].shape[1]
+    dims = [a.shape[0] for a in A]
+    offs = np.concatenate([[0], np.cumsum([R * I for I in dims])])
+    R2 = R * R
+    H = np.zeros((offs[-1], offs[-1]))
+    for n in range(N):
+        for m in range(N):
+            blk = -np.kron(np.eye(R), A[n]) @ St[n * R2:(n + 1) * R2, m * R2:(m + 1) * R2] @ \
+                np.kron(np.eye(R), A[m].T)
+            if n == m:
+                blk = blk + np.kron(Gt[n], np.eye(dims[n]))
+            H[offs[n]:offs[n + 1], offs[m]:offs[m + 1]] = blk
+    return H
+
+
+def hinv_diag(A, Gt, St) -> np.ndarray:
+    """Diagonal of H_mu^{-1} from Theorem 4's blocks, entry by entry in the
+    parameter order of Eq. vecV (A^(n)[i, r] at i + I_n r of block n):
+    Gt^(n)[r, r] - sum_{s, s'} A^(n)[i, s] St^(n,n)[s + R r, s' + R r] A^(n)[i, s']."""
+    N, R = len(A), A[0].shape[1]
+    R2 = R * R
+    out = []
+    for n in range(N):
+        I = A[n].shape[0]
+        Snn = St[n * R2:(n + 1) * R2, n * R2:(n + 1) * R2]
+        d = np.empty(I * R)
+        for r in range(R):
+            blk = Snn[r * R:(r + 1) * R, r * R:(r + 1) * R]
+            for i in range(I):
+                d[i + I * r] = Gt[n][r, r] - A[n][i] @ blk @ A[n][i]
+        out.append(d)
+    return np.concatenate(out)
+
+
+def sae(A_true, A_est):
+    """Squared angular errors alpha^2 of Eq. MedSAE per mode and component
+    after matching the components' order: the permutation pi maximises
+    sum_r sum_n |cos(a_r^(n), ahat_pi(r)^(n))| (a linear assignment), and
+    alpha_r^(n) = arccos |cos(a_r^(n), ahat_pi(r)^(n))| (reading: the absolute
+    value, since CP determines a component's sign only up to flips that
+    cancel across modes).  Returns (alpha2 N x R, pi)."""
+    from scipy.optimize import linear_sum_assignment
+    N, R = len(A_true), A_true[0].shape[1]
+    cos = np.empty((N, R, R))
+    for n in range(N):
+        a = A_true[n] / np.linalg.norm(A_true[n], axis=0)
+        b = A_est[n] / np.linalg.norm(A_est[n], axis=0)
+        cos[n] = np.abs(a.T @ b)
+    score = cos.sum(axis=0)
+    rows, pi = linear_sum_assignment(-score)
+    alpha2 = np.empty((N, R))
+    for n in range(N):
+        for r in range(R):
+            alpha2[n, r] = math.acos(min(1.0, cos[n, r, pi[r]])) ** 2
+    return alpha2, pi
+
+
+def medsae(alpha2_runs) -> float:
+    """MedSAE (Eq. MedSAE) in dB: 10 log10 of the median of the squared
+    angular errors over every run, mode and component given."""
+    v = np.concatenate([np.ravel(a) for a in alpha2_runs])
+    return 10.0 * math.log10(float(np.median(v)))

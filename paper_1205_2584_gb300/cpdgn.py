@@ -86,6 +86,12 @@ _sig = {
                      ctypes.c_int, _vp, _vp],
     "cp_tensor_split": [_vp, ctypes.c_int64, _vp, _vp],
     "cp_selftest_wait_timeout": [ctypes.c_int64, _vp],
+    "cp_hosvd_workspace_bytes": [ctypes.POINTER(Shape), ctypes.POINTER(_sz)],
+    "cp_hosvd": [ctypes.POINTER(Shape), _vp, _vp, ctypes.c_int, _vp, _sz, _vp],
+    "cp_hinv_workspace_bytes": [ctypes.POINTER(Shape), ctypes.POINTER(_sz)],
+    "cp_hinv_blocks": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
+    "cp_hinv_diag": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp],
+    "cp_sae": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp],
     "cp_spd_invert_f32": [ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int),
                           _vp],
 }
@@ -458,3 +464,59 @@ class Batch:
 def selftest_wait_timeout(limit_ns: int = 1_000_000, stream=None):
     """cp_selftest_wait_timeout: one bounded device wait that runs out (see the header)."""
     _check(_lib.cp_selftest_wait_timeout(int(limit_ns), _stream(stream)), "cp_selftest_wait_timeout")
+
+
+def hosvd(shape: Shape, Y: torch.Tensor, a: Optional[torch.Tensor] = None, iters: int = 30, stream=None):
+    """cp_hosvd: HOSVD initial factors into `a` (allocated if None); returns a."""
+    R = shape.R
+    T = sum(shape.I[n] for n in range(shape.N))
+    if a is None:
+        a = torch.empty(R * T, dtype=torch.float64, device=Y.device)
+    nb = _sz(0)
+    _check(_lib.cp_hosvd_workspace_bytes(ctypes.byref(shape), ctypes.byref(nb)), "cp_hosvd_workspace_bytes")
+    ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=Y.device)
+    _check(_lib.cp_hosvd(ctypes.byref(shape), _ptr(Y), _ptr(a), int(iters), _ptr(ws), ws.numel(), _stream(stream)),
+           "cp_hosvd")
+    return a
+
+
+def hinv_blocks(shape: Shape, a: torch.Tensor, mu: float, stream=None):
+    """cp_hinv_blocks: Theorem 4's (Gt, St) of (J^T J + mu I)^{-1} at `a`;
+    returns (Gt, St, info) device tensors."""
+    N, R = shape.N, shape.R
+    n = N * R * R
+    Gt = torch.empty(N * R * R, dtype=torch.float64, device=a.device)
+    St = torch.empty(n * n, dtype=torch.float64, device=a.device)
+    info = torch.zeros(1, dtype=torch.int32, device=a.device)
+    mu_t = torch.tensor([float(mu)], dtype=torch.float64, device=a.device)
+    nb = _sz(0)
+    _check(_lib.cp_hinv_workspace_bytes(ctypes.byref(shape), ctypes.byref(nb)), "cp_hinv_workspace_bytes")
+    ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=a.device)
+    _check(_lib.cp_hinv_blocks(ctypes.byref(shape), _ptr(a), _ptr(mu_t), _ptr(Gt), _ptr(St), _ptr(info), _ptr(ws),
+                               ws.numel(), _stream(stream)), "cp_hinv_blocks")
+    return Gt, St, info
+
+
+def hinv_diag(shape: Shape, a: torch.Tensor, Gt: torch.Tensor, St: torch.Tensor, stream=None):
+    out = torch.empty_like(a)
+    _check(_lib.cp_hinv_diag(ctypes.byref(shape), _ptr(a), _ptr(Gt), _ptr(St), _ptr(out), _stream(stream)),
+           "cp_hinv_diag")
+    return out
+
+
+def sae(shape: Shape, a_true: torch.Tensor, a_est: torch.Tensor, stream=None):
+    """cp_sae: (alpha2 as N x R, perm) device tensors."""
+    alpha2 = torch.empty(shape.N * shape.R, dtype=torch.float64, device=a_true.device)
+    perm = torch.empty(shape.R, dtype=torch.int32, device=a_true.device)
+    _check(_lib.cp_sae(ctypes.byref(shape), _ptr(a_true), _ptr(a_est), _ptr(alpha2), _ptr(perm), _stream(stream)),
+           "cp_sae")
+    return alpha2.view(shape.N, shape.R), perm
+
+
+def medsae_db(alpha2_runs) -> float:
+    """MedSAE (dB): 10 log10 of the median of the squared angular errors of
+    every run given (host-side reduction of cp_sae outputs)."""
+    import math
+    import numpy as np
+    v = np.concatenate([np.ravel(torch.as_tensor(x).double().cpu().numpy()) for x in alpha2_runs])
+    return 10.0 * math.log10(float(np.median(v)))

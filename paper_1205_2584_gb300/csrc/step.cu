@@ -473,9 +473,13 @@ static int solve_core(const Dims& d, const Bufs& B, double* core64, const float*
                              rdone, s));
     }
     if (core64) {
-      // the refinement missed 1e-14 ||b|| (an ill-conditioned core: collinear
-      // factors at small mu) or the float32 inverse failed: float64 Cholesky
-      k_refine_verdict<<<1, 32, 0, s>>>(nrm, K, 1e-28, skip, B.info + IN_INFO32, B.info + IN_SKIP64);
+      // the refinement missed its target (an ill-conditioned core: collinear
+      // factors at small mu) or the float32 inverse failed: float64 Cholesky.
+      // Target: 1e-14 ||b|| for a float64 tensor; 1e-8 ||b|| for float32 and
+      // bfloat16 tensors, whose gradient blocks carry float32-level rounding
+      // already (a tighter core solve would not make the step more accurate)
+      const double tol2 = (d.y_dtype == CP_F64) ? 1e-28 : 1e-16;
+      k_refine_verdict<<<1, 32, 0, s>>>(nrm, K, tol2, skip, B.info + IN_INFO32, B.info + IN_SKIP64);
       CP_TRY(solve_core_f64(d, B, core64, tmo, B.info + IN_SKIP64, s, true));
     }
   }

@@ -597,3 +597,62 @@ def test_sign_fix_convention():
     assert np.array_equal(V[:, 0], -U[:, 0]) and np.array_equal(V[:, 1], -U[:, 1])
     with pytest.raises(ValueError):
         O.hosvd_factors(np.zeros((2, 3, 4)), 3)
+
+
+# ------------------------------------------------- Theorem 4 and MedSAE
+
+
+@pytest.mark.parametrize("dims,R,mu", [((3, 4, 5), 2, 0.7), ((4, 3, 5, 3), 2, 0.2), ((5, 6), 3, 1.3)])
+def test_theorem4_blocks_give_the_inverse_damped_hessian(dims, R, mu):
+    """Eq. fastblock assembled from Theorem 4's blocks equals (J^T J + mu I)^{-1}
+    formed from the explicit Jacobian (Lemma 2); the diagonal helper equals
+    its diagonal."""
+    p = synth.make_problem(70 + R, dims, R, snr_db=30)
+    Gt, St = O.hinv_blocks(p.init, mu)
+    H = O.hinv_from_blocks(p.init, Gt, St)
+    J = O.jacobian(p.init)
+    ref = np.linalg.inv(J.T @ J + mu * np.eye(J.shape[1]))
+    assert _rel(H, ref) < 1e-10
+    assert _rel(O.hinv_diag(p.init, Gt, St), np.diag(ref)) < 1e-10
+    # St is symmetric (H is) and its size is N^2 R^4 entries, Gt N R^2
+    assert _rel(St, St.T) < 1e-12
+
+
+def test_sae_zero_for_permuted_scaled_sign_flipped_copy():
+    rng = np.random.default_rng(80)
+    A = [rng.standard_normal((I, 4)) for I in (6, 7, 8)]
+    perm = np.array([2, 0, 3, 1])
+    sc = [np.array([2.0, -1.0, 0.5, -3.0]), np.array([1.0, -1.0, 4.0, 1.0]), np.array([0.5, 1.0, -0.5, 2.0])]
+    B = [A[n][:, perm] * sc[n][None, :] for n in range(3)]
+    a2, pi = O.sae(A, B)
+    assert np.allclose(a2, 0.0, atol=1e-14)
+    assert np.array_equal(perm[pi], np.arange(4))
+
+
+def test_sae_known_angle_and_assignment_bruteforce():
+    """One column rotated by a known angle theta: alpha^2 = theta^2 there;
+    the matching equals the best permutation found by enumeration."""
+    rng = np.random.default_rng(81)
+    A = [np.linalg.qr(rng.standard_normal((I, 5)))[0] for I in (9, 8, 7)]
+    theta = 0.3
+    B = [a.copy() for a in A]
+    B[1][:, 2] = math.cos(theta) * A[1][:, 2] + math.sin(theta) * np.linalg.qr(
+        np.column_stack([A[1], rng.standard_normal(8)]))[0][:, 5]
+    a2, pi = O.sae(A, B)
+    assert a2[1, 2] == pytest.approx(theta ** 2, rel=1e-12)
+    assert np.allclose(np.delete(a2.ravel(), 1 * 5 + 2), 0.0, atol=1e-14)
+    # assignment optimality against enumeration on noisy estimates
+    for seed in range(5):
+        r = np.random.default_rng(90 + seed)
+        Ah = [a + 0.6 * r.standard_normal(a.shape) for a in A]
+        a2, pi = O.sae(A, Ah)
+        cos = np.stack([np.abs((A[n] / np.linalg.norm(A[n], axis=0)).T @ (Ah[n] / np.linalg.norm(Ah[n], axis=0)))
+                        for n in range(3)]).sum(axis=0)
+        best = max(itertools.permutations(range(5)), key=lambda q: sum(cos[i, q[i]] for i in range(5)))
+        assert sum(cos[i, pi[i]] for i in range(5)) == pytest.approx(sum(cos[i, best[i]] for i in range(5)),
+                                                                      rel=1e-12)
+
+
+def test_medsae_definition():
+    a2 = [np.array([[1e-4, 4e-4], [9e-4, 1e-2]]), np.array([[2.5e-3]])]
+    assert O.medsae(a2) == pytest.approx(10 * math.log10(9e-4), rel=1e-12)
