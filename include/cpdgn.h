@@ -55,7 +55,8 @@ extern "C" {
  * The planes are the direct operands of the tensor-core pass, so this form is
  * accepted only where that pass applies: N = 3, I_1 a multiple of 8 (the
  * buffer must be 16-byte aligned); other shapes return CP_EINVAL. */
-enum cp_dtype { CP_F64 = 0, CP_F32 = 1, CP_BF16 = 2, CP_BF16X2 = 3 };
+enum cp_dtype { CP_F64 = 0, CP_F32 = 1, CP_BF16 = 2, CP_BF16X2 = 3,
+                CP_C128 = 4 /* complex128 (re, im interleaved): cp_cstate_* calls only */ };
 
 /* status codes */
 enum cp_code {
@@ -407,6 +408,38 @@ int cp_hinv_diag(const cp_shape* shape, const double* a, const double* Gt, const
  * MedSAE in dB is 10 log10 of the median of alpha2 over the runs compared. */
 int cp_sae(const cp_shape* shape, const double* a_true, const double* a_est, double* alpha2, int* perm,
            void* stream);
+
+/* ---- complex-valued tensors (Sec. 5, Theorems 5-8) ---- */
+
+/* The damped Gauss-Newton iteration for a complex tensor (shape->y_dtype =
+ * CP_C128: complex128, real and imaginary parts interleaved, first index
+ * fastest) with complex factors (the factor vector a of Eq. vecV in complex128
+ * entries, 2 R T doubles).  Each trial: C^(n) = A^(n)H A^(n),
+ * Gamma^(n,m) = Hadamard_{k != n,m} C^(k) (Theorem 5); the gradient blocks
+ * G_n = E_(n) conj(KR_n) = Y_(n) conj(KR_n) - A^(n) Gamma^(n)T (Theorem 7) from
+ * one pass over the tensor; the fast step of Theorem 8 in Hermitian positive
+ * definite core form (core = I + S^H K S, S_n = U_n kron L_n,
+ * Gamma^(n) + mu I = L_G L_G^H, U_n = L_G^{-H}, C^(n) = L_n L_n^H), the core
+ * solved in float64 through its real symmetric representation
+ * [[Re, -Im], [Im, Re]] by the float64 Cholesky; the update
+ * Delta_n = (G_n - A^(n) F_n) Gt^(n)T, Gt^(n) = (Gamma^(n) + mu I)^{-1} (the
+ * matrix form of Theorem 8's damped inverse acts through its transpose);
+ * the Sec. 4.6 control with gain-ratio denominator Re(Delta^H (g + mu Delta))
+ * and normalisation by real positive scales.  Limits: R <= 16, I_1 <= 256,
+ * N R^2 <= 3200 (CP_EINVAL otherwise).  Same conventions as the real state:
+ * caller-owned factor buffer and workspace, all work on `stream`, no host
+ * synchronisation, later steps no-ops once stopped (cp_status.core_f64 = 1). */
+typedef struct cp_cstate cp_cstate;
+int cp_cstate_workspace_bytes(const cp_shape* shape, size_t* bytes);
+int cp_cstate_create(const cp_shape* shape, const cp_opts* opts, double* a, void* ws, size_t ws_bytes,
+                     cp_cstate** out);
+int cp_cstate_destroy(cp_cstate* st);
+int cp_cstate_init(cp_cstate* st, const void* Y, void* stream);
+int cp_cdgn_step(cp_cstate* st, const void* Y, void* stream);
+cp_status* cp_cstate_status(cp_cstate* st);
+/* 0 = gradient blocks at the current factors, 1 = last step, 5 = trial factors
+ * (complex128, R T entries each); NULL for another id. */
+double* cp_cstate_buffer(cp_cstate* st, int id);
 
 /* ---- batched form: many small decompositions in one persistent launch ---- */
 

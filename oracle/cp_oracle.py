@@ -617,3 +617,166 @@ def medsae(alpha2_runs) -> float:
     angular errors over every run, mode and component given."""
     v = np.concatenate([np.ravel(a) for a in alpha2_runs])
     return 10.0 * math.log10(float(np.median(v)))
+
+
+# ---------------------------------------------------------------------------
+# Complex-valued tensors (Sec. 5: Theorems 5-8).  The model Y_hat is
+# holomorphic in the factors; the damped Gauss-Newton update is
+# a <- a + (J^H J + mu I)^{-1} J^H vec(Y - Y_hat) (Eq. GaussNewton_v_complex).
+# C^(n) = A^(n)H A^(n) (Hermitian), Gamma^(n,m) = Hadamard_{k != n,m} C^(k).
+# ---------------------------------------------------------------------------
+
+
+def cgrams(A):
+    """Complex Gramians: C^(n) = A^(n)H A^(n), Gamma^(n,m), Gamma (Theorem 5)."""
+    N = len(A)
+    R = A[0].shape[1]
+    C = [a.conj().T @ a for a in A]
+    G = np.empty((N, N, R, R), dtype=complex)
+    for n in range(N):
+        for m in range(N):
+            P = np.ones((R, R), dtype=complex)
+            for k in range(N):
+                if k != n and k != m:
+                    P = P * C[k]
+            G[n, m] = P
+    full = np.ones((R, R), dtype=complex)
+    for k in range(N):
+        full = full * C[k]
+    return Grams(C=C, Gamma_nm=G, Gamma_all=full)
+
+
+def cgradient_blocks(Y, A):
+    """g = J^H vec(E) in blocks Y_(n) (Hadamard... ) : G_n = Y_(n) conj(KR_n) - A^(n) Gamma^(n)T
+    (Theorem 7, Eq. grad_complex_g)."""
+    g = cgrams(A)
+    return [unfold(Y, n) @ kr_except(A, n).conj() - A[n] @ g.Gamma(n).T for n in range(len(A))]
+
+
+def ctextbook_step(Y, A, mu: float):
+    """(J^H J + mu I)^{-1} J^H vec(Y - Y_hat) with the holomorphic Jacobian of
+    Lemma 2 (complex factors), solved by Cholesky (Hermitian)."""
+    J = jacobian(A)
+    e = vec(Y - cp_full(A))
+    H = J.conj().T @ J
+    gvec = J.conj().T @ e
+    d = sla.cho_solve(sla.cho_factor(H + mu * np.eye(H.shape[0]), lower=True), gvec)
+    return split_params(d, [a.shape[0] for a in A], A[0].shape[1])
+
+
+def cflm_step(Y, A, mu: float):
+    """Theorem 8's fast complex step.  Kronecker-form Psi_mu = blkdiag(Gt^(n)
+    kron C^(n)) with Gt^(n) = (Gamma^(n) + mu I)^{-1} (Eq. ZiGZ_LM_cplx),
+    K = [P_R diag(vec Gamma^(n,m))] (Theorem 6), B_mu = K (I + Psi_mu K)^{-1};
+    in matrix form the damped inverse acts as X -> X Gt^(n)T (reading: the
+    printed Gt of the matrix-form update is the transpose (Gamma^(n)T + mu I)^{-1},
+    the form the paper's own earlier statement of the update uses), so
+      A_mu = Y_(n) conj(KR_n) Gt^T,   w_n = vec(A^(n)H (A_mu - A^(n) Gamma^(n)T Gt^T)),
+      Delta_n = A_mu + A^(n) (I - (F_n + Gamma^(n)T) Gt^T) - A^(n)   (Eq. fast_low_LM1-complex).
+    Returns (delta, G, Gt, w, f)."""
+    N = len(A)
+    R = A[0].shape[1]
+    R2 = R * R
+    g = cgrams(A)
+    P = perm_PR(R)
+    K = np.zeros((N * R2, N * R2), dtype=complex)
+    for n in range(N):
+        for m in range(N):
+            if n != m:
+                K[n * R2:(n + 1) * R2, m * R2:(m + 1) * R2] = P @ np.diag(vec(g.Gamma_nm[n, m]))
+    Gt = [np.linalg.inv(g.Gamma(n) + mu * np.eye(R)) for n in range(N)]
+    Psi = sla.block_diag(*[np.kron(Gt[n], g.C[n]) for n in range(N)])
+    M = [unfold(Y, n) @ kr_except(A, n).conj() for n in range(N)]
+    parts = []
+    for n in range(N):
+        A_mu = M[n] @ Gt[n].T
+        parts.append(vec(A[n].conj().T @ (A_mu - A[n] @ g.Gamma(n).T @ Gt[n].T)))
+    w = np.concatenate(parts)
+    f = K @ np.linalg.solve(np.eye(N * R2) + Psi @ K, w)
+    delta, G = [], []
+    for n in range(N):
+        Fn = unvec(f[n * R2:(n + 1) * R2], (R, R))
+        A_mu = M[n] @ Gt[n].T
+        An = A_mu + A[n] @ (np.eye(R) - (Fn + g.Gamma(n).T) @ Gt[n].T)
+        delta.append(An - A[n])
+        G.append(M[n] - A[n] @ g.Gamma(n).T)
+    return delta, G, Gt, w, f
+
+
+def clm_fit(Y, A0, mu0: Optional[float] = None, max_iter: int = 200, tol: float = 0.0,
+            normalize: bool = True, tau: float = 1e-3, mu_max: float = 1e30) -> LMResult:
+    """The LM loop of lm_fit for complex tensors with the fast complex step:
+    the same acceptance, Nielsen rule and stop tests; the gain ratio's
+    denominator is Re(Delta^H (g + mu Delta)) (the decrease of ||E||^2 the
+    linear model predicts); normalisation spreads each component's norm
+    equally over the modes with real positive scales (phases kept); mu_0 =
+    tau max diag(H) = tau max_n max Gamma^(n)[r, r]."""
+    A = [np.array(a, dtype=complex, copy=True) for a in A0]
+    ynorm = float(np.linalg.norm(Y))
+    if mu0 is None:
+        g0 = cgrams(A)
+        mu = tau * max(float(np.max(np.real(np.diag(g0.Gamma(n))))) for n in range(len(A)))
+    else:
+        mu = float(mu0)
+    nu = 2.0
+
+    def r2(A):
+        E = Y - cp_full(A)
+        return float(np.sum(np.abs(E) ** 2))
+    rr = r2(A)
+    hist, accepted, stop, it = [], 0, "max_iter", 0
+    while it < max_iter:
+        it += 1
+        delta, G, _, _, _ = cflm_step(Y, A, mu)
+        An = [a + d for a, d in zip(A, delta)]
+        rn = r2(An)
+        den = sum(float(np.real(np.vdot(d, gn + mu * d))) for d, gn in zip(delta, G))
+        rho = (rr - rn) / den if den > 0 else 0.0
+        if rn < rr:
+            eo, en = math.sqrt(rr) / ynorm, math.sqrt(rn) / ynorm
+            if normalize:
+                norms = np.stack([np.linalg.norm(a, axis=0) for a in An])
+                for r in range(An[0].shape[1]):
+                    if np.all(norms[:, r] > 0):
+                        t = float(np.prod(norms[:, r])) ** (1.0 / len(An))
+                        for n in range(len(An)):
+                            An[n][:, r] = An[n][:, r] * (t / norms[n, r])
+            A, rr = An, rn
+            accepted += 1
+            mu, nu = nielsen_update(mu, nu, rho)
+            hist.append(en)
+            if eo > 0 and abs(eo - en) / eo < tol:
+                stop = "tol"
+                break
+        else:
+            mu, nu = nielsen_update(mu, nu, rho)
+            hist.append(math.sqrt(rr) / ynorm)
+        if mu > mu_max:
+            stop = "mu_max"
+            break
+    return LMResult(A=A, resid2=rr, rel_err=math.sqrt(rr) / ynorm, iters=it, accepted=accepted, mu=mu,
+                    stop=stop, history=hist)
+
+
+def cspd_core(A, mu: float):
+    """The Hermitian positive definite core of the complex step (the complex
+    counterpart of spd_core): S_n = U_n kron L_n with Gamma^(n) + mu I =
+    L_G L_G^H, U_n = L_G^{-H}, C^(n) = L_n L_n^H, so S S^H = Psi_mu; core =
+    I + S^H K S and f = K w - K S core^{-1} S^H K w.  Returns (core, S, K)."""
+    g = cgrams(A)
+    N, R = len(A), A[0].shape[1]
+    R2 = R * R
+    S = []
+    for n in range(N):
+        LG = np.linalg.cholesky(g.Gamma(n) + mu * np.eye(R))
+        U = np.linalg.inv(LG).conj().T
+        LC = np.linalg.cholesky(g.C[n])
+        S.append(np.kron(U, LC))
+    S = sla.block_diag(*S)
+    P = perm_PR(R)
+    K = np.zeros((N * R2, N * R2), dtype=complex)
+    for n in range(N):
+        for m in range(N):
+            if n != m:
+                K[n * R2:(n + 1) * R2, m * R2:(m + 1) * R2] = P @ np.diag(vec(g.Gamma_nm[n, m]))
+    return np.eye(N * R2) + S.conj().T @ K @ S, S, K

@@ -23,12 +23,12 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 CP_MAX_N = 8
 CP_MAX_R = 32
-CP_F64, CP_F32, CP_BF16, CP_BF16X2 = 0, 1, 2, 3
+CP_F64, CP_F32, CP_BF16, CP_BF16X2, CP_C128 = 0, 1, 2, 3, 4
 CP_CORE_F64, CP_CORE_MIXED = 0, 1
 CODES = {0: "CP_OK", 1: "CP_EINVAL", 2: "CP_ENOTSPD", 3: "CP_ENONFINITE", 4: "CP_ETIMEOUT",
          5: "CP_ENOMEM", 6: "CP_ECUDA"}
 STOP = {0: "running", 1: "tol", 2: "mu_max", 3: "max_iter", 4: "error"}
-DTYPES = {"f64": CP_F64, "f32": CP_F32, "bf16": CP_BF16, "bf16x2": CP_BF16X2}
+DTYPES = {"f64": CP_F64, "f32": CP_F32, "bf16": CP_BF16, "bf16x2": CP_BF16X2, "c128": CP_C128}
 # storage dtype of Y; the CP_BF16X2 form holds 2 J bfloat16 values (hi plane, lo plane)
 TORCH_DTYPE = {CP_F64: torch.float64, CP_F32: torch.float32, CP_BF16: torch.bfloat16, CP_BF16X2: torch.bfloat16}
 
@@ -92,6 +92,11 @@ _sig = {
     "cp_hinv_blocks": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
     "cp_hinv_diag": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp],
     "cp_sae": [ctypes.POINTER(Shape), _vp, _vp, _vp, _vp, _vp],
+    "cp_cstate_workspace_bytes": [ctypes.POINTER(Shape), ctypes.POINTER(_sz)],
+    "cp_cstate_create": [ctypes.POINTER(Shape), ctypes.POINTER(Opts), _vp, _vp, _sz, ctypes.POINTER(_vp)],
+    "cp_cstate_destroy": [_vp],
+    "cp_cstate_init": [_vp, _vp, _vp],
+    "cp_cdgn_step": [_vp, _vp, _vp],
     "cp_spd_invert_f32": [ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int),
                           _vp],
 }
@@ -103,6 +108,10 @@ _lib.cp_state_status.argtypes = [_vp]
 _lib.cp_state_status.restype = _vp
 _lib.cp_state_buffer.argtypes = [_vp, ctypes.c_int]
 _lib.cp_state_buffer.restype = _vp
+_lib.cp_cstate_status.argtypes = [_vp]
+_lib.cp_cstate_status.restype = _vp
+_lib.cp_cstate_buffer.argtypes = [_vp, ctypes.c_int]
+_lib.cp_cstate_buffer.restype = _vp
 
 
 class BatchProblem(ctypes.Structure):
@@ -116,7 +125,8 @@ _lib.cp_batch_check.restype = ctypes.c_int
 _lib.cp_batch_layout.argtypes = [ctypes.POINTER(BatchProblem), ctypes.c_int, ctypes.POINTER(_sz)]
 _lib.cp_batch_layout.restype = ctypes.c_int
 
-EXPORTED = list(_sig) + ["cp_state_status", "cp_state_buffer", "cp_batch_check", "cp_batch_layout"]
+EXPORTED = list(_sig) + ["cp_state_status", "cp_state_buffer", "cp_batch_check", "cp_batch_layout",
+                         "cp_cstate_status", "cp_cstate_buffer"]
 
 
 def _check(rc: int, what: str):
@@ -520,3 +530,72 @@ def medsae_db(alpha2_runs) -> float:
     import numpy as np
     v = np.concatenate([np.ravel(torch.as_tensor(x).double().cpu().numpy()) for x in alpha2_runs])
     return 10.0 * math.log10(float(np.median(v)))
+
+
+# ---------------------------------------------------------------------------
+# complex-valued tensors (cp_cstate_*)
+# ---------------------------------------------------------------------------
+
+def ctensor_to_device(Y, device="cuda") -> torch.Tensor:
+    """Complex numpy tensor -> complex128 device vector in vec order (first index fastest)."""
+    import numpy as np
+    flat = np.asarray(Y, dtype=np.complex128).ravel(order="F")
+    return torch.from_numpy(flat.copy()).to(device)
+
+
+def cfactors_to_device(factors, device="cuda") -> torch.Tensor:
+    parts = [torch.as_tensor(f, dtype=torch.complex128).t().contiguous().reshape(-1) for f in factors]
+    return torch.cat(parts).to(device)
+
+
+class CState:
+    """One complex decomposition whose factors, damping and counters live on the GPU."""
+
+    BUF_G, BUF_DELTA, BUF_AT = 0, 1, 5
+
+    def __init__(self, shape: Shape, a: torch.Tensor, *, mu0: float = -1.0, tau: float = 1e-3, tol: float = 0.0,
+                 mu_max: float = 1e30, max_iter: int = 1000, normalize: bool = True):
+        assert a.dtype == torch.complex128 and a.is_cuda and a.is_contiguous()
+        self.shape, self.a = shape, a
+        self.opts = Opts(mu0=mu0, tau=tau, tol=tol, mu_max=mu_max, max_iter=max_iter,
+                         normalize=1 if normalize else 0, core_mode=CP_CORE_F64, refine_iters=0)
+        nb = _sz(0)
+        _check(_lib.cp_cstate_workspace_bytes(ctypes.byref(shape), ctypes.byref(nb)), "cp_cstate_workspace_bytes")
+        self.ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=a.device)
+        h = ctypes.c_void_p()
+        _check(_lib.cp_cstate_create(ctypes.byref(shape), ctypes.byref(self.opts), _ptr(a), _ptr(self.ws),
+                                     self.ws.numel(), ctypes.byref(h)), "cp_cstate_create")
+        self._h = h
+        self._status_ptr = _lib.cp_cstate_status(h)
+        self._host_status = torch.empty(128, dtype=torch.uint8).pin_memory()
+
+    def init(self, Y, stream=None):
+        _check(_lib.cp_cstate_init(self._h, _ptr(Y), _stream(stream)), "cp_cstate_init")
+
+    def step(self, Y, stream=None):
+        _check(_lib.cp_cdgn_step(self._h, _ptr(Y), _stream(stream)), "cp_cdgn_step")
+
+    def status(self, stream=None) -> dict:
+        st = stream if stream is not None else torch.cuda.current_stream()
+        off = self._status_ptr - self.ws.data_ptr()
+        self._host_status.copy_(self.ws[off:off + 128], non_blocking=True)
+        st.synchronize()
+        d = Status.from_buffer_copy(bytes(self._host_status.numpy())).as_dict()
+        d["stop_reason"] = STOP.get(d["stop"], d["stop"])
+        return d
+
+    def buffer(self, which: int, count: int) -> torch.Tensor:
+        p = _lib.cp_cstate_buffer(self._h, which)
+        off = p - self.ws.data_ptr()
+        return self.ws[off:off + 16 * count].view(torch.complex128)
+
+    def close(self):
+        if self._h:
+            _lib.cp_cstate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

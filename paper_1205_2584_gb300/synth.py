@@ -218,3 +218,33 @@ def config5_requests(seed: int = 0, rate: float = 200.0, seconds: float = 60.0):
         c = float(rng.uniform(0.0, 0.95))
         out.append((t, int(rng.integers(0, 2**31 - 1)), dims, R, c))
     return out
+
+
+def make_complex_problem(seed: int, dims: Sequence[int], R: int, *, snr_db: Optional[float] = 30.0,
+                         collinearity: Sequence[float] = (), init_scale: float = 1.0) -> Problem:
+    """Complex-valued recipe (Sec. 6, complex tensors: factors with random
+    real and imaginary parts): A^(n) = X + i Y with X, Y iid N(0, 1/2) (or
+    collinear columns built the same way from complex Gaussian vectors),
+    Y = sum of outer products + complex Gaussian noise with E|noise|^2 =
+    sigma^2 at the requested SNR (sigma from ||Y||_F as for real tensors);
+    complex N(0, 1/2) + i N(0, 1/2) initial factors."""
+    rng = rng_for(seed)
+    N = len(dims)
+    factors = []
+    for n, I in enumerate(dims):
+        Z = (rng.standard_normal((I, R)) + 1j * rng.standard_normal((I, R))) / math.sqrt(2.0)
+        if n < len(collinearity) and collinearity[n] > 0:
+            c = collinearity[n]
+            b = (rng.standard_normal((I, 1)) + 1j * rng.standard_normal((I, 1))) / math.sqrt(2.0)
+            Z = math.sqrt(c) * b + math.sqrt(1.0 - c) * Z
+        factors.append(Z)
+    letters = string.ascii_lowercase[:N]
+    spec = ",".join(f"{l}z" for l in letters) + "->" + letters
+    Y = np.einsum(spec, *factors, optimize=True)
+    if snr_db is not None:
+        sigma = 10.0 ** (-snr_db / 20.0) * np.linalg.norm(Y) / math.sqrt(Y.size)
+        Y = Y + sigma * (rng.standard_normal(Y.shape) + 1j * rng.standard_normal(Y.shape)) / math.sqrt(2.0)
+    init = [init_scale * (rng.standard_normal((I, R)) + 1j * rng.standard_normal((I, R))) / math.sqrt(2.0)
+            for I in dims]
+    return Problem(Y=np.asfortranarray(Y), true_factors=factors, init=init, R=R, dtype="c128", mu0=None,
+                   name=f"complex-{dims}-R{R}")

@@ -1,0 +1,128 @@
+"""Complex-valued tensors (Sec. 5, Theorems 5-8) through the C ABI
+(cp_cstate_*), against the oracle's complex routines (pinned against the
+textbook complex step with the explicit holomorphic Jacobian).
+
+  * the gradient blocks of the pass (E_(n) conj(KR_n)) to 1e-12;
+  * one step against the oracle's fast complex step to 1e-10 (N = 2..4,
+    R up to 16, ragged I_1 up to 256);
+  * LM runs to the stop rule: final epsilon within 1e-10 of the oracle's;
+  * noiseless exact-rank complex tensors fitted to epsilon < 1e-10;
+  * the paper's complex workload shape (70^4, R = 5): one step at full size
+    against the oracle.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import cp_oracle as O  # noqa: E402
+from paper_1205_2584_gb300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def cp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1205_2584_gb300 import cpdgn
+    return cpdgn
+
+
+def rel(a, b):
+    a = np.concatenate([np.ravel(np.asarray(x)) for x in a])
+    b = np.concatenate([np.ravel(np.asarray(x)) for x in b])
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def split(cp, t, dims, R):
+    out, off = [], 0
+    x = t.cpu().numpy()
+    for I in dims:
+        out.append(x[off:off + I * R].reshape(R, I).T.copy())
+        off += I * R
+    return out
+
+
+CASES = [((6, 7, 8), 3, 0.5), ((12, 10), 4, 1.0), ((5, 6, 4, 5), 2, 0.3), ((40, 9, 11), 8, 2.0),
+         ((256, 5, 6), 16, 3.0), ((33, 20, 21), 16, 0.7)]
+
+
+@pytest.mark.parametrize("dims,R,mu", CASES)
+def test_complex_step_matches_oracle(cp, dims, R, mu):
+    p = synth.make_complex_problem(220 + R, dims, R, snr_db=25)
+    shape = cp.make_shape(dims, R, "c128")
+    Y = cp.ctensor_to_device(p.Y)
+    a = cp.cfactors_to_device(p.init)
+    st = cp.CState(shape, a, mu0=mu, max_iter=10, normalize=False)
+    st.init(Y)
+    torch.cuda.synchronize()
+    nA = R * sum(dims)
+    G = split(cp, st.buffer(cp.CState.BUF_G, nA), dims, R)
+    assert rel(G, O.cgradient_blocks(p.Y, p.init)) < 1e-12
+    st.step(Y)
+    torch.cuda.synchronize()
+    s = st.status()
+    assert s["info"] == 0 and s["iters"] == 1
+    d = split(cp, st.buffer(cp.CState.BUF_DELTA, nA), dims, R)
+    ref, _, _, _, _ = O.cflm_step(p.Y, p.init, mu)
+    assert rel(d, ref) < 1e-10
+    st.close()
+
+
+@pytest.mark.parametrize("dims,R", [((10, 11, 12), 3), ((8, 7, 6, 5), 2)])
+def test_complex_lm_run_matches_oracle(cp, dims, R):
+    p = synth.make_complex_problem(230 + R, dims, R, snr_db=30, collinearity=(0.6,))
+    shape = cp.make_shape(dims, R, "c128")
+    Y = cp.ctensor_to_device(p.Y)
+    a = cp.cfactors_to_device(p.init)
+    st = cp.CState(shape, a, mu0=-1.0, tol=1e-9, max_iter=300)
+    st.init(Y)
+    for _ in range(300):
+        st.step(Y)
+        if st.status()["stop"] != 0:
+            break
+    s = st.status()
+    ref = O.clm_fit(p.Y, p.init, mu0=None, max_iter=300, tol=1e-9)
+    assert s["stop_reason"] == ref.stop
+    assert s["iters"] == ref.iters
+    assert abs(s["rel_err"] - ref.rel_err) <= 1e-10 * ref.rel_err
+
+
+def test_complex_noiseless_converges(cp):
+    p = synth.make_complex_problem(240, (9, 8, 10), 3, snr_db=None)
+    rng = np.random.default_rng(241)
+    A0 = [x + 0.3 * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)) for x in p.true_factors]
+    shape = cp.make_shape(p.dims, p.R, "c128")
+    Y = cp.ctensor_to_device(p.Y)
+    st = cp.CState(shape, cp.cfactors_to_device(A0), mu0=1.0, max_iter=300)
+    st.init(Y)
+    for _ in range(300):
+        st.step(Y)
+    assert st.status()["rel_err"] < 1e-10
+
+
+def test_complex_paper_shape_one_step(cp):
+    """70^4, R = 5 (the paper's complex experiments): one step at full size."""
+    p = synth.make_complex_problem(250, (70, 70, 70, 70), 5, snr_db=30)
+    shape = cp.make_shape(p.dims, p.R, "c128")
+    Y = cp.ctensor_to_device(p.Y)
+    a = cp.cfactors_to_device(p.init)
+    mu = 0.8
+    st = cp.CState(shape, a, mu0=mu, max_iter=10, normalize=False)
+    st.init(Y)
+    st.step(Y)
+    torch.cuda.synchronize()
+    d = split(cp, st.buffer(cp.CState.BUF_DELTA, p.R * sum(p.dims)), p.dims, p.R)
+    ref, _, _, _, _ = O.cflm_step(p.Y, p.init, mu)
+    assert rel(d, ref) < 1e-10
+    s = st.status()
+    E = p.Y - O.cp_full(p.init)
+    assert s["resid2"] == pytest.approx(float(np.sum(np.abs(E) ** 2)), rel=1e-12)
+
+
+def test_complex_rejects_real_calls_and_limits(cp):
+    with pytest.raises(cp.CPError):
+        cp.make_shape((4, 5, 6), 2, "c128") and cp.workspace_bytes(cp.make_shape((4, 5, 6), 2, "c128"))
+    with pytest.raises(cp.CPError):
+        cp.CState(cp.make_shape((300, 5, 6), 2, "c128"),
+                  torch.zeros(2 * 311, dtype=torch.complex128, device="cuda"))

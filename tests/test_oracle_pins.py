@@ -13,6 +13,7 @@ import os
 
 import numpy as np
 import pytest
+import scipy.linalg as sla
 
 from oracle import cp_oracle as O
 from paper_1205_2584_gb300 import synth
@@ -656,3 +657,73 @@ def test_sae_known_angle_and_assignment_bruteforce():
 def test_medsae_definition():
     a2 = [np.array([[1e-4, 4e-4], [9e-4, 1e-2]]), np.array([[2.5e-3]])]
     assert O.medsae(a2) == pytest.approx(10 * math.log10(9e-4), rel=1e-12)
+
+
+# --------------------------------------------------------- complex (Sec. 5)
+
+
+@pytest.mark.parametrize("dims,R,mu", [((4, 5, 6), 3, 0.3), ((5, 6), 2, 2.0), ((3, 4, 3, 4), 2, 0.8)])
+def test_complex_fast_step_equals_textbook(dims, R, mu):
+    """Theorem 8 (with the reading of the damped inverse as Gt^T in matrix
+    form) against (J^H J + mu I)^{-1} J^H e from the explicit holomorphic
+    Jacobian."""
+    p = synth.make_complex_problem(200 + R, dims, R, snr_db=20)
+    ref = O.ctextbook_step(p.Y, p.init, mu)
+    d, G, Gt, w, f = O.cflm_step(p.Y, p.init, mu)
+    assert _rel(d, ref) < 1e-10
+
+
+def test_complex_hessian_and_gradient_structure():
+    """Theorems 5-7: J^H J = G + Z K Z^H with G = blkdiag(Gamma^(n) kron I),
+    Z = blkdiag(I_R kron A^(n)), K^(n,m) = P_R diag(vec Gamma^(n,m)); the
+    gradient blocks Y_(n) conj(KR_n) - A^(n) Gamma^(n)T equal J^H vec(E)."""
+    p = synth.make_complex_problem(210, (3, 4, 5), 2, snr_db=20)
+    A = p.init
+    J = O.jacobian(A)
+    H = J.conj().T @ J
+    g = O.cgrams(A)
+    R = 2
+    Gm = sla.block_diag(*[np.kron(g.Gamma(n), np.eye(a.shape[0])) for n, a in enumerate(A)])
+    Z = sla.block_diag(*[np.kron(np.eye(R), a) for a in A])
+    _, _, K = O.cspd_core(A, 1.0)
+    assert _rel(H, Gm + Z @ K @ Z.conj().T) < 1e-13
+    e = O.vec(p.Y - O.cp_full(A))
+    assert _rel(O.join_params(O.cgradient_blocks(p.Y, A)), J.conj().T @ e) < 1e-13
+
+
+def test_complex_gradient_finite_differences():
+    """f(a) = ||Y - Y_hat(a)||^2: a real step h e_k changes f by -2 h Re g_k,
+    an imaginary step i h e_k by -2 h Im g_k (g = J^H vec(E))."""
+    p = synth.make_complex_problem(211, (3, 4, 3), 2, snr_db=10)
+    dims, R = p.dims, p.R
+    a = O.join_params(p.init)
+    g = O.join_params(O.cgradient_blocks(p.Y, p.init))
+    f = lambda x: float(np.sum(np.abs(p.Y - O.cp_full(O.split_params(x, dims, R))) ** 2))
+    h = 1e-6
+    for k in (0, 5, 11, len(a) - 1):
+        e = np.zeros_like(a)
+        e[k] = h
+        dre = (f(a + e) - f(a - e)) / (2 * h)
+        dim = (f(a + 1j * e) - f(a - 1j * e)) / (2 * h)
+        assert dre == pytest.approx(-2 * g[k].real, rel=1e-6, abs=1e-8)
+        assert dim == pytest.approx(-2 * g[k].imag, rel=1e-6, abs=1e-8)
+
+
+def test_complex_spd_core_gives_the_fast_f():
+    p = synth.make_complex_problem(212, (5, 6, 4), 3, snr_db=20)
+    mu = 0.4
+    core, S, K = O.cspd_core(p.init, mu)
+    assert _rel(core, core.conj().T) < 1e-14
+    assert np.min(np.linalg.eigvalsh(core)) > 0
+    _, _, _, w, f = O.cflm_step(p.Y, p.init, mu)
+    Kw = K @ w
+    fs = Kw - K @ (S @ np.linalg.solve(core, S.conj().T @ Kw))
+    assert _rel(fs, f) < 1e-12
+
+
+def test_complex_noiseless_converges():
+    p = synth.make_complex_problem(213, (7, 8, 6), 3, snr_db=None)
+    rng = np.random.default_rng(214)
+    A0 = [a + 0.3 * (rng.standard_normal(a.shape) + 1j * rng.standard_normal(a.shape)) for a in p.true_factors]
+    res = O.clm_fit(p.Y, A0, mu0=1.0, max_iter=300)
+    assert res.rel_err < 1e-10
