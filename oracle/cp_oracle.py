@@ -664,7 +664,7 @@ def ctextbook_step(Y, A, mu: float):
     return split_params(d, [a.shape[0] for a in A], A[0].shape[1])
 
 
-def cflm_step(Y, A, mu: float):
+def cflm_step(Y, A, mu: float, G=None):
     """Theorem 8's fast complex step.  Kronecker-form Psi_mu = blkdiag(Gt^(n)
     kron C^(n)) with Gt^(n) = (Gamma^(n) + mu I)^{-1} (Eq. ZiGZ_LM_cplx),
     K = [P_R diag(vec Gamma^(n,m))] (Theorem 6), B_mu = K (I + Psi_mu K)^{-1};
@@ -673,6 +673,7 @@ def cflm_step(Y, A, mu: float):
     the form the paper's own earlier statement of the update uses), so
       A_mu = Y_(n) conj(KR_n) Gt^T,   w_n = vec(A^(n)H (A_mu - A^(n) Gamma^(n)T Gt^T)),
       Delta_n = A_mu + A^(n) (I - (F_n + Gamma^(n)T) Gt^T) - A^(n)   (Eq. fast_low_LM1-complex).
+    G (optional): the gradient blocks to use (M_n = G_n + A^(n) Gamma^(n)T).
     Returns (delta, G, Gt, w, f)."""
     N = len(A)
     R = A[0].shape[1]
@@ -686,7 +687,10 @@ def cflm_step(Y, A, mu: float):
                 K[n * R2:(n + 1) * R2, m * R2:(m + 1) * R2] = P @ np.diag(vec(g.Gamma_nm[n, m]))
     Gt = [np.linalg.inv(g.Gamma(n) + mu * np.eye(R)) for n in range(N)]
     Psi = sla.block_diag(*[np.kron(Gt[n], g.C[n]) for n in range(N)])
-    M = [unfold(Y, n) @ kr_except(A, n).conj() for n in range(N)]
+    if G is None:
+        M = [unfold(Y, n) @ kr_except(A, n).conj() for n in range(N)]
+    else:
+        M = [G[n] + A[n] @ g.Gamma(n).T for n in range(N)]
     parts = []
     for n in range(N):
         A_mu = M[n] @ Gt[n].T
