@@ -521,73 +521,146 @@ __global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// The pivot chain is the sequential part of the inversion.  Each pivot block
-// is inverted by one 256-thread CTA that keeps the block in registers (4 x 4
-// entries per thread); an elimination step broadcasts the pivot row and
-// column through shared memory (one float4 each per thread); a step costs
-// about 0.1 us of dependent latency (barrier, shared-memory round trip,
-// reciprocal, multiply-add), so a 64 x 64 inverse takes about 7 us.  For
-// sweep k + 1 the same CTA first forms its pivot tile
+// The pivot chain is the sequential part of the inversion.  Each 64 x 64
+// pivot block is inverted by one 256-thread CTA (invert64_blocked below:
+// two warp-level 32-step eliminations and four 32^3 products).  For sweep
+// k + 1 the same CTA first forms its pivot tile
 // X = A[k+1,k+1] - A[k+1,k] (P_k^{-1} A[k,k+1]) from sweep k's input, so it
 // runs concurrently with sweep k's row panel and update.
 // ---------------------------------------------------------------------------
-__device__ void gj_invert_tile(float (&x)[4][4], int kb, float (*prow)[GJB], float (*pcol)[GJB], int* bad) {
-  __shared__ float pv[GJB];                                    // pivots, checked at the end
-  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
-#pragma unroll 4
-  for (int p = 0; p < kb; ++p) {
-    const int par = p & 1;
-    const int hp = p >> 2, lp = p & 3;
-    if (bi == hp) {
-      float4 t;
-      t.x = x[lp][0];
-      t.y = x[lp][1];
-      t.z = x[lp][2];
-      t.w = x[lp][3];
-      *reinterpret_cast<float4*>(&prow[par][4 * bj]) = t;
+// In-place Gauss-Jordan inverse of the 32 x 32 block at (o, o) of M (no
+// pivoting: the block is symmetric positive definite) by one warp: lane j
+// keeps column j in registers; at step p lane p publishes its column through
+// shared memory (double-buffered, so one __syncwarp per step) and every lane
+// updates its column:  M[i][j] -= M[i][p] M[p][j] / M[p][p] (i, j != p),
+// M[p][j] /= M[p][p], M[i][p] = -M[i][p] / M[p][p], M[p][p] = 1 / M[p][p].
+// The pivots are recorded in piv (checked by the caller).
+__device__ void warp_gj32(float (*M)[GJP], int o, float (*colbuf)[32], float* piv) {
+  const int lane = threadIdx.x & 31;
+  float c[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) c[i] = M[o + i][o + lane];
+#pragma unroll
+  for (int p = 0; p < 32; ++p) {
+    float* cb = colbuf[p & 1];
+    if (lane == p) {
+#pragma unroll
+      for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4*>(cb + i) = make_float4(c[i], c[i + 1], c[i + 2], c[i + 3]);
     }
-    if (bj == hp) {
-      float4 t;
-      t.x = x[0][lp];
-      t.y = x[1][lp];
-      t.z = x[2][lp];
-      t.w = x[3][lp];
-      *reinterpret_cast<float4*>(&pcol[par][4 * bi]) = t;
+    __syncwarp();
+    float col[32];
+#pragma unroll
+    for (int i = 0; i < 32; i += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(cb + i);
+      col[i] = v.x;
+      col[i + 1] = v.y;
+      col[i + 2] = v.z;
+      col[i + 3] = v.w;
     }
-    __syncthreads();
-    const float piv = prow[par][p];
-    if (threadIdx.x == 0) pv[p] = piv;
-    const float dinv = recip(piv);
-    const float4 c4 = *reinterpret_cast<const float4*>(&pcol[par][4 * bi]);
-    const float4 r4 = *reinterpret_cast<const float4*>(&prow[par][4 * bj]);
-    const float c[4] = {c4.x, c4.y, c4.z, c4.w};
-    const float r[4] = {r4.x * dinv, r4.y * dinv, r4.z * dinv, r4.w * dinv};
+    const float pv = col[p];
+    if (lane == 0) piv[p] = pv;
+    const float inv = recip(pv);
+    if (lane == p) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+      for (int i = 0; i < 32; ++i) c[i] = (i == p) ? inv : -col[i] * inv;
+    } else {
+      const float rp = c[p] * inv;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) x[u][v] = fmaf(-c[u], r[v], x[u][v]);
-    if (bi == hp) {                  // row p -> scaled pivot row
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (lp == 0) x[0][v] = r[v];
-        else if (lp == 1) x[1][v] = r[v];
-        else if (lp == 2) x[2][v] = r[v];
-        else x[3][v] = r[v];
-    }
-    if (bj == hp) {                  // column p -> -col / piv; the pivot itself -> 1 / piv
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float val = (bi == hp && u == lp) ? dinv : -c[u] * dinv;
-        if (lp == 0) x[u][0] = val;
-        else if (lp == 1) x[u][1] = val;
-        else if (lp == 2) x[u][2] = val;
-        else x[u][3] = val;
-      }
+      for (int i = 0; i < 32; ++i) c[i] = (i == p) ? rp : fmaf(-col[i], rp, c[i]);
     }
   }
-  // check the recorded pivots once, after the elimination
+#pragma unroll
+  for (int i = 0; i < 32; ++i) M[o + i][o + lane] = c[i];
+}
+
+// Inverse of the 64 x 64 SPD tile x (4 x 4 per thread, layout of load_block)
+// in place, by 2 x 2 blocks [[A, B], [B^T, D]] of 32 x 32:
+//   A <- A^{-1} (one warp), T = A^{-1} B, S = D - B^T T, S <- S^{-1} (one warp),
+//   X12 = -T S^{-1}, X11 = A^{-1} - X12 T^T, X21 = X12^T, X22 = S^{-1}.
+// The chain is two 32-step warp eliminations (no CTA barrier inside them)
+// plus four 32^3 products over the CTA.  M, T: 64 x GJP and 32 x GJP float
+// scratch in shared memory.  *bad receives the first non-positive or
+// non-finite pivot, 1-based, of the two eliminations (A's pivots are the
+// tile's first 32; S's are the Schur pivots of the last 32).
+__device__ void invert64_blocked(float (&x)[4][4], int kb, float (*M)[GJP], float (*T)[GJP], int* bad) {
+  __shared__ __align__(16) float colbuf[2][32];
+  __shared__ float pv[GJB];
+  const int tid = threadIdx.x, bi = tid % 16, bj = tid / 16;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) M[4 * bi + u][4 * bj + v] = x[u][v];
   __syncthreads();
-  if (threadIdx.x < kb && !(pv[threadIdx.x] > 0.f && isfinite(pv[threadIdx.x]))) atomicMin(bad, threadIdx.x + 1);
+  if (tid < 32) warp_gj32(M, 0, colbuf, pv);
+  __syncthreads();
+  // T = A^{-1} B: entry (i, j), i, j < 32, four per thread
+  {
+    float t[4];
+    const int j = tid % 32, i0 = (tid / 32) * 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float s = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) s = fmaf(M[i0 + u][k], M[k][32 + j], s);
+      t[u] = s;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) T[i0 + u][j] = t[u];
+  }
+  __syncthreads();
+  // S = D - B^T T (into D's place)
+  {
+    const int j = tid % 32, i0 = (tid / 32) * 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float s = M[32 + i0 + u][32 + j];
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) s = fmaf(-M[k][32 + i0 + u], T[k][j], s);
+      M[32 + i0 + u][32 + j] = s;
+    }
+  }
+  __syncthreads();
+  if (tid < 32) warp_gj32(M, 32, colbuf, pv + 32);
+  __syncthreads();
+  // X12 = -T S^{-1} (into B's place; B is no longer needed)
+  {
+    float t[4];
+    const int j = tid % 32, i0 = (tid / 32) * 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float s = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) s = fmaf(-T[i0 + u][k], M[32 + k][32 + j], s);
+      t[u] = s;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) M[i0 + u][32 + j] = t[u];
+  }
+  __syncthreads();
+  // X11 = A^{-1} - X12 T^T, X21 = X12^T
+  {
+    float t[4];
+    const int j = tid % 32, i0 = (tid / 32) * 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float s = M[i0 + u][j];
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) s = fmaf(-M[i0 + u][32 + k], T[j][k], s);
+      t[u] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      M[i0 + u][j] = t[u];
+      M[32 + j][i0 + u] = M[i0 + u][32 + j];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) x[u][v] = M[4 * bi + u][4 * bj + v];
+  if (tid < kb && !(pv[tid] > 0.f && isfinite(pv[tid]))) atomicMin(bad, tid + 1);
   __syncthreads();
 }
 
@@ -604,10 +677,10 @@ __device__ __forceinline__ void pad_identity(float (&x)[4][4], int kb) {
 // Invert x (pivot tile kk) and write P^{-1} to Pinv (64 x 64) and into tile
 // (kk, kk) of D.
 __device__ void pivot_store(float (&x)[4][4], int64_t n, int kk, int kb, float* Pinv, float* D, int* info,
-                            float (*prow)[GJB], float (*pcol)[GJB], int* bad) {
+                            float (*M)[GJP], float (*T)[GJP], int* bad) {
   if (threadIdx.x == 0) *bad = GJB + 1;
   __syncthreads();
-  gj_invert_tile(x, kb, prow, pcol, bad);
+  invert64_blocked(x, kb, M, T, bad);
   if (threadIdx.x == 0 && *bad <= GJB && info) atomicCAS(info, 0, kk * GJB + *bad);
   store_block(x, Pinv, GJB, 0, 0);
   store_block(x, D, n, int64_t(kk) * GJB, int64_t(kk) * GJB);
@@ -618,13 +691,13 @@ template <typename T>
 __global__ void __launch_bounds__(GJT) k_gj_pivot(const T* A, T* D, int64_t n, int k, T* Pinv, int* info,
                                                   const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
+  __shared__ __align__(16) float Ms[GJB][GJP], Ts[GJB / 2][GJP];
   __shared__ int bad;
   const int kb = int((n - int64_t(k) * GJB) < GJB ? (n - int64_t(k) * GJB) : GJB);
   float x[4][4];
   load_block(A, n, int64_t(k) * GJB, int64_t(k) * GJB, x);
   pad_identity(x, kb);
-  pivot_store(x, n, k, kb, Pinv, D, info, prow, pcol, &bad);
+  pivot_store(x, n, k, kb, Pinv, D, info, Ms, Ts, &bad);
 }
 
 // Pivot of sweep k + 1 during sweep k, from sweep k's input A and pivot
@@ -639,7 +712,6 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, c
                                                        int* info, const int* skip) {
   if (skip && *skip) return;
   __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP], L2s[GJB][GJP];
-  __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
   __shared__ int bad;
   const int k1 = k + 1;
   const int kb = int((n - int64_t(k1) * GJB) < GJB ? (n - int64_t(k1) * GJB) : GJB);
@@ -660,7 +732,8 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, c
   __syncthreads();
   tile_fma<GJB>(L2s, Rs, x);
   pad_identity(x, kb);
-  pivot_store(x, n, k1, kb, Pinv_next, A, info, prow, pcol, &bad);
+  __syncthreads();                                   // Ls and L2s are free: scratch of the inversion
+  pivot_store(x, n, k1, kb, Pinv_next, A, info, Ls, L2s, &bad);
 }
 
 // Invert the n x n SPD matrix A (full storage, column-major); B is the second

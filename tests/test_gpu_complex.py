@@ -111,6 +111,9 @@ def test_complex_paper_shape_one_step(cp):
     st = cp.CState(shape, a, mu0=mu, max_iter=10, normalize=False)
     st.init(Y)
     torch.cuda.synchronize()
+    E = p.Y - O.cp_full(p.init)
+    assert st.status()["resid2"] == pytest.approx(float(np.sum(np.abs(E) ** 2)), rel=1e-12)
+    del E
     nA = p.R * sum(p.dims)
     G = split(cp, st.buffer(cp.CState.BUF_G, nA), p.dims, p.R)
     G_ref = O.cgradient_blocks(p.Y, p.init)
@@ -131,9 +134,6 @@ def test_complex_paper_shape_one_step(cp):
     # moves the step through the damped system; recorded, held loosely
     ref2, _, _, _, _ = O.cflm_step(p.Y, p.init, mu)
     assert rel(d, ref2) < 1e-7
-    s = st.status()
-    E = p.Y - O.cp_full(p.init)
-    assert s["resid2"] == pytest.approx(float(np.sum(np.abs(E) ** 2)), rel=1e-12)
 
 
 def test_complex_rejects_real_calls_and_limits(cp):
