@@ -18,10 +18,10 @@
 // update.  That CTA reserves nearly all of its SM's shared memory, so no tile
 // CTA shares the SM with it.
 //
-// Tile products.  The pivot kernels (256 threads on a 64 x 64 tile): thread
-// (bi, bj) owns rows 4 bi .. 4 bi + 3 and columns 4 bj .. 4 bj + 3, so each
+// Tile products.  The pivot kernels (128 threads on a 64 x 64 tile): thread
+// (bi, bj) owns rows 4 bi .. 4 bi + 3 and columns 8 bj .. 8 bj + 7, so each
 // k-step reads one float4 of the left operand (stored column by column, rows
-// contiguous) and one float4 of the right operand (stored row by row) for 16
+// contiguous) and two float4 of the right operand (stored row by row) for 32
 // multiply-adds.  The row panel, the update and the identity elimination work
 // on 64 x 32 half tiles (twice as many CTAs as tiles, which spreads a sweep
 // evenly over the SMs) with 64 threads: thread (bi, bj) owns rows
@@ -36,7 +36,7 @@
 namespace cpdgn {
 
 constexpr int GJB = 64;           // panel / tile height
-constexpr int GJT = 256;          // threads of a 64 x 64 tile CTA: 16 x 16 threads, 4 x 4 entries each
+constexpr int GJT = 128;          // threads of a 64 x 64 tile CTA: 16 x 8 threads, 4 x 8 entries each
 constexpr int GJH = 32;           // width of a half tile
 constexpr int GJTH = 64;          // threads of a 64 x 32 half-tile CTA: 8 x 8 threads, 8 x 4 entries each
 constexpr int GJP = GJB + 4;      // padded row length in shared memory (keeps float4 alignment)
@@ -49,6 +49,18 @@ constexpr int kPivotReserve = 168 * 1024;
 // Reciprocal of a pivot.  The float32 inverse only preconditions the float64
 // refinement, so the fast intrinsic division (about 2 ulp) is accurate enough.
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+
+// Programmatic dependent launch.  The sweep kernels are launched with the
+// programmatic-serialisation attribute, so a kernel's CTAs may be scheduled
+// while its predecessor on the stream still runs.  Every CTA first waits
+// (griddepcontrol.wait) until the predecessor has completed and its writes
+// are visible, before it reads anything (the skip flag included) or exits,
+// so each kernel completes after its predecessor and the ordering is
+// transitive.  It then lets its own successor be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
 
 // S[c][r] = sgn * A(r0 + r, c0 + c) for r, c < 64 (zero outside n x n): a
 // 64 x 64 left operand stored column by column.  Global reads are coalesced
@@ -65,27 +77,27 @@ __device__ __forceinline__ void load_cols(const float* A, int64_t n, int64_t r0,
   }
 }
 
-// S[r][c] = A(r0 + r, c0 + c) for r < 64, c < TC: a right operand stored row
-// by row.  4 TC threads.
-template <int TC>
-__device__ __forceinline__ void load_rows(const float* A, int64_t n, int64_t r0, int64_t c0, float (*S)[TC + 4]) {
+// S[r][c] = A(r0 + r, c0 + c) for r, c < 64: a right operand stored row by
+// row.  Global reads are coalesced along r.  NT threads.
+template <int NT>
+__device__ __forceinline__ void load_rows(const float* A, int64_t n, int64_t r0, int64_t c0, float (*S)[GJP]) {
 #pragma unroll
-  for (int q = 0; q < GJB / 4; ++q) {
-    const int e = int(threadIdx.x) + q * 4 * TC;
+  for (int q = 0; q < GJB * GJB / NT; ++q) {
+    const int e = int(threadIdx.x) + q * NT;
     const int r = e % GJB, c = e / GJB;
     const int64_t gr = r0 + r, gc = c0 + c;
     S[r][c] = (gr < n && gc < n) ? A[gr + n * gc] : 0.f;
   }
 }
 
-// the thread's 4 x 4 block of the 64 x TC tile at (r0, c0); entries outside n x n read as 0
-__device__ __forceinline__ void load_block(const float* A, int64_t n, int64_t r0, int64_t c0, float (&x)[4][4]) {
+// the thread's 4 x 8 block of the 64 x 64 tile at (r0, c0); entries outside n x n read as 0
+__device__ __forceinline__ void load_block(const float* A, int64_t n, int64_t r0, int64_t c0, float (&x)[4][8]) {
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
   const int64_t rr = r0 + 4 * bi;
   const bool vec = (n % 4 == 0) && (rr + 3 < n);
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int64_t c = c0 + 4 * bj + v;
+  for (int v = 0; v < 8; ++v) {
+    const int64_t c = c0 + 8 * bj + v;
     if (c >= n) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) x[u][v] = 0.f;
@@ -102,13 +114,13 @@ __device__ __forceinline__ void load_block(const float* A, int64_t n, int64_t r0
   }
 }
 
-__device__ __forceinline__ void store_block(const float (&x)[4][4], float* B, int64_t n, int64_t r0, int64_t c0) {
+__device__ __forceinline__ void store_block(const float (&x)[4][8], float* B, int64_t n, int64_t r0, int64_t c0) {
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
   const int64_t rr = r0 + 4 * bi;
   const bool vec = (n % 4 == 0) && (rr + 3 < n);
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int64_t c = c0 + 4 * bj + v;
+  for (int v = 0; v < 8; ++v) {
+    const int64_t c = c0 + 8 * bj + v;
     if (c >= n) continue;
     if (vec) {
       *reinterpret_cast<float4*>(B + rr + n * c) = make_float4(x[0][v], x[1][v], x[2][v], x[3][v]);
@@ -120,26 +132,26 @@ __device__ __forceinline__ void store_block(const float (&x)[4][4], float* B, in
   }
 }
 
-__device__ __forceinline__ void zero_block(float (&x)[4][4]) {
+__device__ __forceinline__ void zero_block(float (&x)[4][8]) {
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) x[u][v] = 0.f;
+    for (int v = 0; v < 8; ++v) x[u][v] = 0.f;
 }
 
-// x += L R with L = Lc (64 x 64, columns) and R = Rr (64 x TC, rows).
-template <int TC>
-__device__ __forceinline__ void tile_fma(const float (*Lc)[GJP], const float (*Rr)[TC + 4], float (&x)[4][4]) {
+// x += L R with L = Lc (64 x 64, columns) and R = Rr (64 x 64, rows).
+__device__ __forceinline__ void tile_fma(const float (*Lc)[GJP], const float (*Rr)[GJP], float (&x)[4][8]) {
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
 #pragma unroll 8
   for (int l = 0; l < GJB; ++l) {
     const float4 a = *reinterpret_cast<const float4*>(&Lc[l][4 * bi]);
-    const float4 b = *reinterpret_cast<const float4*>(&Rr[l][4 * bj]);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    const float4 b0 = *reinterpret_cast<const float4*>(&Rr[l][8 * bj]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Rr[l][8 * bj + 4]);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) x[u][v] = fmaf(av[u], bv[v], x[u][v]);
+      for (int v = 0; v < 8; ++v) x[u][v] = fmaf(av[u], bv[v], x[u][v]);
   }
 }
 
@@ -343,6 +355,7 @@ constexpr int kTileSmem = 2 * GJB * GJP * 4;   // (Ls, Rc) or (Ls, Rs)
 template <typename T, bool ASYNC>
 __global__ void __launch_bounds__(GJTH) k_gj_rowpanel(const T* A, T* B, int64_t n, int k, const T* Pinv,
                                                       const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   extern __shared__ __align__(16) float dsm[];
   float (*Ps)[GJP] = reinterpret_cast<float (*)[GJP]>(dsm);
@@ -388,6 +401,7 @@ __global__ void __launch_bounds__(GJTH) k_gj_rowpanel(const T* A, T* B, int64_t 
 template <typename T, bool ASYNC>
 __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n, int k, const T* Pinv,
                                                     int skip_pivot, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   extern __shared__ __align__(16) float dsm[];
   float (*Ls)[GJP] = reinterpret_cast<float (*)[GJP]>(dsm);
@@ -456,6 +470,7 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
 constexpr int kIdentSmem = 2 * 2 * GJB * GJP * 4;   // two stages of (Ls, Rc)
 template <typename T, bool ASYNC>
 __global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t n, int kb0, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   extern __shared__ __align__(16) float dsm[];
   const int nt = int((n + GJB - 1) / GJB);
@@ -521,166 +536,83 @@ __global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// The pivot chain is the sequential part of the inversion.  Each 64 x 64
-// pivot block is inverted by one 256-thread CTA (invert64_blocked below:
-// two warp-level 32-step eliminations and four 32^3 products).  For sweep
-// k + 1 the same CTA first forms its pivot tile
+// The pivot chain is the sequential part of the inversion.  Each pivot block
+// is inverted by one 128-thread CTA that keeps the block in registers (4 x 8
+// entries per thread); an elimination step broadcasts the pivot row (two
+// float4 per owning thread) and column (one float4) through shared memory,
+// double-buffered, so one barrier per step.  A step is about 170 cycles of
+// dependent latency (store, barrier, load, reciprocal, multiply-add), so a
+// 64 x 64 inverse takes about 6 us; the 256-thread 4 x 4 layout took about
+// 240 cycles a step, its extra instructions per step lying on the chain.
+// For sweep k + 1 the same CTA first forms its pivot tile
 // X = A[k+1,k+1] - A[k+1,k] (P_k^{-1} A[k,k+1]) from sweep k's input, so it
 // runs concurrently with sweep k's row panel and update.
 // ---------------------------------------------------------------------------
-// In-place Gauss-Jordan inverse of the 32 x 32 block at (o, o) of M (no
-// pivoting: the block is symmetric positive definite) by one warp: lane j
-// keeps column j in registers; at step p lane p publishes its column through
-// shared memory (double-buffered, so one __syncwarp per step) and every lane
-// updates its column:  M[i][j] -= M[i][p] M[p][j] / M[p][p] (i, j != p),
-// M[p][j] /= M[p][p], M[i][p] = -M[i][p] / M[p][p], M[p][p] = 1 / M[p][p].
-// The pivots are recorded in piv (checked by the caller).
-__device__ void warp_gj32(float (*M)[GJP], int o, float (*colbuf)[32], float* piv) {
-  const int lane = threadIdx.x & 31;
-  float c[32];
+// All 64 steps run, in groups of 8 so that the row and column a step reads
+// sit at compile-time offsets of the owning threads' registers.  Rows and
+// columns beyond kb hold the identity (pad_identity), and a step on such a
+// unit row/column leaves the tile unchanged; only the first kb pivots are
+// checked.
+__device__ void gj_invert_tile(float (&x)[4][8], int kb, float (*prow)[GJB], float (*pcol)[GJB], int* bad) {
+  __shared__ float pv[GJB];                                    // pivots, checked at the end
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+  for (int g = 0; g < GJB / 8; ++g) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) c[i] = M[o + i][o + lane];
+    for (int q = 0; q < 8; ++q) {
+      const int p = 8 * g + q, par = q & 1, lr = q & 3;
+      const bool orow = (bi == (p >> 2)), ocol = (bj == g);   // owners of row p / column p
+      if (orow) {
+        *reinterpret_cast<float4*>(&prow[par][8 * bj]) = make_float4(x[lr][0], x[lr][1], x[lr][2], x[lr][3]);
+        *reinterpret_cast<float4*>(&prow[par][8 * bj + 4]) = make_float4(x[lr][4], x[lr][5], x[lr][6], x[lr][7]);
+      }
+      if (ocol) *reinterpret_cast<float4*>(&pcol[par][4 * bi]) = make_float4(x[0][q], x[1][q], x[2][q], x[3][q]);
+      __syncthreads();
+      const float piv = prow[par][p];
+      if (threadIdx.x == 0) pv[p] = piv;
+      const float dinv = recip(piv);
+      const float4 c4 = *reinterpret_cast<const float4*>(&pcol[par][4 * bi]);
+      const float4 r0 = *reinterpret_cast<const float4*>(&prow[par][8 * bj]);
+      const float4 r1 = *reinterpret_cast<const float4*>(&prow[par][8 * bj + 4]);
+      const float c[4] = {c4.x, c4.y, c4.z, c4.w};
+      const float r[8] = {r0.x * dinv, r0.y * dinv, r0.z * dinv, r0.w * dinv,
+                          r1.x * dinv, r1.y * dinv, r1.z * dinv, r1.w * dinv};
 #pragma unroll
-  for (int p = 0; p < 32; ++p) {
-    float* cb = colbuf[p & 1];
-    if (lane == p) {
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4*>(cb + i) = make_float4(c[i], c[i + 1], c[i + 2], c[i + 3]);
-    }
-    __syncwarp();
-    float col[32];
+        for (int v = 0; v < 8; ++v) x[u][v] = fmaf(-c[u], r[v], x[u][v]);
+      if (orow) {                    // row p -> scaled pivot row
 #pragma unroll
-    for (int i = 0; i < 32; i += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(cb + i);
-      col[i] = v.x;
-      col[i + 1] = v.y;
-      col[i + 2] = v.z;
-      col[i + 3] = v.w;
-    }
-    const float pv = col[p];
-    if (lane == 0) piv[p] = pv;
-    const float inv = recip(pv);
-    if (lane == p) {
+        for (int v = 0; v < 8; ++v) x[lr][v] = r[v];
+      }
+      if (ocol) {                    // column p -> -col / piv; the pivot itself -> 1 / piv
 #pragma unroll
-      for (int i = 0; i < 32; ++i) c[i] = (i == p) ? inv : -col[i] * inv;
-    } else {
-      const float rp = c[p] * inv;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) c[i] = (i == p) ? rp : fmaf(-col[i], rp, c[i]);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 32; ++i) M[o + i][o + lane] = c[i];
-}
-
-// Inverse of the 64 x 64 SPD tile x (4 x 4 per thread, layout of load_block)
-// in place, by 2 x 2 blocks [[A, B], [B^T, D]] of 32 x 32:
-//   A <- A^{-1} (one warp), T = A^{-1} B, S = D - B^T T, S <- S^{-1} (one warp),
-//   X12 = -T S^{-1}, X11 = A^{-1} - X12 T^T, X21 = X12^T, X22 = S^{-1}.
-// The chain is two 32-step warp eliminations (no CTA barrier inside them)
-// plus four 32^3 products over the CTA.  M, T: 64 x GJP and 32 x GJP float
-// scratch in shared memory.  *bad receives the first non-positive or
-// non-finite pivot, 1-based, of the two eliminations (A's pivots are the
-// tile's first 32; S's are the Schur pivots of the last 32).
-__device__ void invert64_blocked(float (&x)[4][4], int kb, float (*M)[GJP], float (*T)[GJP], int* bad) {
-  __shared__ __align__(16) float colbuf[2][32];
-  __shared__ float pv[GJB];
-  const int tid = threadIdx.x, bi = tid % 16, bj = tid / 16;
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) M[4 * bi + u][4 * bj + v] = x[u][v];
-  __syncthreads();
-  if (tid < 32) warp_gj32(M, 0, colbuf, pv);
-  __syncthreads();
-  // T = A^{-1} B: entry (i, j), i, j < 32, four per thread
-  {
-    float t[4];
-    const int j = tid % 32, i0 = (tid / 32) * 4;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float s = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) s = fmaf(M[i0 + u][k], M[k][32 + j], s);
-      t[u] = s;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) T[i0 + u][j] = t[u];
-  }
-  __syncthreads();
-  // S = D - B^T T (into D's place)
-  {
-    const int j = tid % 32, i0 = (tid / 32) * 4;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float s = M[32 + i0 + u][32 + j];
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) s = fmaf(-M[k][32 + i0 + u], T[k][j], s);
-      M[32 + i0 + u][32 + j] = s;
+        for (int u = 0; u < 4; ++u) x[u][q] = (orow && u == lr) ? dinv : -c[u] * dinv;
+      }
     }
   }
+  // check the recorded pivots once, after the elimination
   __syncthreads();
-  if (tid < 32) warp_gj32(M, 32, colbuf, pv + 32);
-  __syncthreads();
-  // X12 = -T S^{-1} (into B's place; B is no longer needed)
-  {
-    float t[4];
-    const int j = tid % 32, i0 = (tid / 32) * 4;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float s = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) s = fmaf(-T[i0 + u][k], M[32 + k][32 + j], s);
-      t[u] = s;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) M[i0 + u][32 + j] = t[u];
-  }
-  __syncthreads();
-  // X11 = A^{-1} - X12 T^T, X21 = X12^T
-  {
-    float t[4];
-    const int j = tid % 32, i0 = (tid / 32) * 4;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float s = M[i0 + u][j];
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) s = fmaf(-M[i0 + u][32 + k], T[j][k], s);
-      t[u] = s;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      M[i0 + u][j] = t[u];
-      M[32 + j][i0 + u] = M[i0 + u][32 + j];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) x[u][v] = M[4 * bi + u][4 * bj + v];
-  if (tid < kb && !(pv[tid] > 0.f && isfinite(pv[tid]))) atomicMin(bad, tid + 1);
+  if (threadIdx.x < kb && !(pv[threadIdx.x] > 0.f && isfinite(pv[threadIdx.x]))) atomicMin(bad, threadIdx.x + 1);
   __syncthreads();
 }
 
 // rows/columns of a partial pivot tile beyond kb become the identity
-__device__ __forceinline__ void pad_identity(float (&x)[4][4], int kb) {
+__device__ __forceinline__ void pad_identity(float (&x)[4][8], int kb) {
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-      if (4 * bi + u >= kb || 4 * bj + v >= kb) x[u][v] = (4 * bi + u == 4 * bj + v) ? 1.f : 0.f;
+    for (int v = 0; v < 8; ++v)
+      if (4 * bi + u >= kb || 8 * bj + v >= kb) x[u][v] = (4 * bi + u == 8 * bj + v) ? 1.f : 0.f;
 }
 
 // Invert x (pivot tile kk) and write P^{-1} to Pinv (64 x 64) and into tile
 // (kk, kk) of D.
-__device__ void pivot_store(float (&x)[4][4], int64_t n, int kk, int kb, float* Pinv, float* D, int* info,
-                            float (*M)[GJP], float (*T)[GJP], int* bad) {
+__device__ void pivot_store(float (&x)[4][8], int64_t n, int kk, int kb, float* Pinv, float* D, int* info,
+                            float (*prow)[GJB], float (*pcol)[GJB], int* bad) {
   if (threadIdx.x == 0) *bad = GJB + 1;
   __syncthreads();
-  invert64_blocked(x, kb, M, T, bad);
+  gj_invert_tile(x, kb, prow, pcol, bad);
   if (threadIdx.x == 0 && *bad <= GJB && info) atomicCAS(info, 0, kk * GJB + *bad);
   store_block(x, Pinv, GJB, 0, 0);
   store_block(x, D, n, int64_t(kk) * GJB, int64_t(kk) * GJB);
@@ -690,14 +622,15 @@ __device__ void pivot_store(float (&x)[4][4], int64_t n, int kk, int kb, float* 
 template <typename T>
 __global__ void __launch_bounds__(GJT) k_gj_pivot(const T* A, T* D, int64_t n, int k, T* Pinv, int* info,
                                                   const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ms[GJB][GJP], Ts[GJB / 2][GJP];
+  __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
   __shared__ int bad;
   const int kb = int((n - int64_t(k) * GJB) < GJB ? (n - int64_t(k) * GJB) : GJB);
-  float x[4][4];
+  float x[4][8];
   load_block(A, n, int64_t(k) * GJB, int64_t(k) * GJB, x);
   pad_identity(x, kb);
-  pivot_store(x, n, k, kb, Pinv, D, info, Ms, Ts, &bad);
+  pivot_store(x, n, k, kb, Pinv, D, info, prow, pcol, &bad);
 }
 
 // Pivot of sweep k + 1 during sweep k, from sweep k's input A and pivot
@@ -710,30 +643,50 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot(const T* A, T* D, int64_t n, i
 template <typename T>
 __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, const T* Pinv, T* Pinv_next,
                                                        int* info, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP], L2s[GJB][GJP];
+  __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
   __shared__ int bad;
   const int k1 = k + 1;
   const int kb = int((n - int64_t(k1) * GJB) < GJB ? (n - int64_t(k1) * GJB) : GJB);
   const int64_t o = int64_t(k) * GJB, o1 = int64_t(k1) * GJB;
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
   load_cols<GJT>(Pinv, GJB, 0, 0, Ls, 1.f);
-  load_rows<GJB>(A, n, o, o1, Rs);                   // A[k, k+1]
+  load_rows<GJT>(A, n, o, o1, Rs);                   // A[k, k+1]
   load_cols<GJT>(A, n, o1, o, L2s, -1.f);            // -A[k+1, k]
-  float x[4][4], t[4][4];
+  float x[4][8], t[4][8];
   load_block(A, n, o1, o1, x);                       // A[k+1, k+1]
   zero_block(t);
   __syncthreads();
-  tile_fma<GJB>(Ls, Rs, t);                          // t = P^{-1} A[k, k+1]
+  tile_fma(Ls, Rs, t);                               // t = P^{-1} A[k, k+1]
   __syncthreads();
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-    *reinterpret_cast<float4*>(&Rs[4 * bi + u][4 * bj]) = make_float4(t[u][0], t[u][1], t[u][2], t[u][3]);
+  for (int u = 0; u < 4; ++u) {
+    *reinterpret_cast<float4*>(&Rs[4 * bi + u][8 * bj]) = make_float4(t[u][0], t[u][1], t[u][2], t[u][3]);
+    *reinterpret_cast<float4*>(&Rs[4 * bi + u][8 * bj + 4]) = make_float4(t[u][4], t[u][5], t[u][6], t[u][7]);
+  }
   __syncthreads();
-  tile_fma<GJB>(L2s, Rs, x);
+  tile_fma(L2s, Rs, x);
   pad_identity(x, kb);
-  __syncthreads();                                   // Ls and L2s are free: scratch of the inversion
-  pivot_store(x, n, k1, kb, Pinv_next, A, info, Ls, L2s, &bad);
+  pivot_store(x, n, k1, kb, Pinv_next, A, info, prow, pcol, &bad);
+}
+
+// Launch with the programmatic-serialisation attribute (see pdl_enter).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 // Invert the n x n SPD matrix A (full storage, column-major); B is the second
@@ -759,16 +712,20 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
       if (cudaFuncSetAttribute(k_gj_identity<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kIdentSmem) != cudaSuccess)
         return CP_ECUDA;
-      k_gj_identity<T, true><<<nt * nt * 2, GJTH, kIdentSmem, s>>>(src, dst, n, k0, skip);
+      if (launch_pdl(k_gj_identity<T, true>, nt * nt * 2, GJTH, kIdentSmem, s, src, dst, n, k0, skip) != cudaSuccess)
+        return CP_ECUDA;
     } else {
-      k_gj_identity<T, false><<<nt * nt * 2, GJTH, (GJB * GJP + GJB * (GJH + 4)) * 4, s>>>(src, dst, n, k0,
-                                                                                           skip);
+      if (launch_pdl(k_gj_identity<T, false>, nt * nt * 2, GJTH, (GJB * GJP + GJB * (GJH + 4)) * 4, s, src, dst, n,
+                     k0, skip) != cudaSuccess)
+        return CP_ECUDA;
     }
     T* t = src;
     src = dst;
     dst = t;
   }
-  k_gj_pivot<T><<<1, GJT, 0, s>>>(src, dst, n, k0, pinv + size_t(k0 & 1) * GJB * GJB, info, skip);
+  if (launch_pdl(k_gj_pivot<T>, 1, GJT, 0, s, src, dst, n, k0, pinv + size_t(k0 & 1) * GJB * GJB, info, skip) !=
+      cudaSuccess)
+    return CP_ECUDA;
   for (int k = k0; k < nt; ++k) {
     T* pk = pinv + size_t(k & 1) * GJB * GJB;
     T* pn = pinv + size_t((k + 1) & 1) * GJB * GJB;
@@ -781,18 +738,23 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
         if (cudaEventRecord(ev_join, side) != cudaSuccess) return CP_ECUDA;
       }
       if (n % 4 == 0) {
-        k_gj_rowpanel<T, true><<<(nt - 1) * 2, GJTH, kTileSmem, s>>>(src, dst, n, k, pk, skip);
-        k_gj_update<T, true><<<(nt - 1) * nt * 2, GJTH, kTileSmem, s>>>(src, dst, n, k, pk,
-                                                                        (next && side) ? 1 : 0, skip);
+        if (launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk, skip) !=
+                cudaSuccess ||
+            launch_pdl(k_gj_update<T, true>, (nt - 1) * nt * 2, GJTH, kTileSmem, s, src, dst, n, k, pk,
+                       (next && side) ? 1 : 0, skip) != cudaSuccess)
+          return CP_ECUDA;
       } else {
-        k_gj_rowpanel<T, false><<<(nt - 1) * 2, GJTH, kTileSmem, s>>>(src, dst, n, k, pk, skip);
-        k_gj_update<T, false><<<(nt - 1) * nt * 2, GJTH, kTileSmem, s>>>(src, dst, n, k, pk,
-                                                                         (next && side) ? 1 : 0, skip);
+        if (launch_pdl(k_gj_rowpanel<T, false>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk, skip) !=
+                cudaSuccess ||
+            launch_pdl(k_gj_update<T, false>, (nt - 1) * nt * 2, GJTH, kTileSmem, s, src, dst, n, k, pk,
+                       (next && side) ? 1 : 0, skip) != cudaSuccess)
+          return CP_ECUDA;
       }
       if (next && side) {
         if (cudaStreamWaitEvent(s, ev_join, 0) != cudaSuccess) return CP_ECUDA;
       } else if (next) {
-        k_gj_pivot<T><<<1, GJT, 0, s>>>(dst, src, n, k + 1, pn, info, skip);
+        if (launch_pdl(k_gj_pivot<T>, 1, GJT, 0, s, dst, src, n, k + 1, pn, info, skip) != cudaSuccess)
+          return CP_ECUDA;
       }
     }
     T* t = src;
