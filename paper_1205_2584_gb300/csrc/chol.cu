@@ -10,9 +10,10 @@
 //  k_chol64 (one persistent launch, one CTA per SM, blocked right-looking
 //  with 32-wide panels).  Per panel k:
 //    phase A  every CTA factors the 32 x 32 diagonal tile in shared memory
-//             (one warp, lane = row, the pivot's reciprocal square root
-//             shared through a shuffle), and solves its share of the panel's
-//             rows X <- X L_kk^{-T} (one warp per row, lane = column);
+//             (the whole CTA, see factor_tile; redundant across CTAs, so no
+//             barrier separates it from the panel) and solves its share of
+//             the panel's rows X <- X L_kk^{-T} (one warp per row, lane =
+//             column); after the barrier CTA 0 stores L_kk;
 //    phase B  the trailing update A_ij -= L_ik L_jk^T over 32 x 32 tiles of
 //             the lower triangle, tiles dealt round-robin to the CTAs;
 //  separated by grid barriers (an arrival counter and a generation word in
