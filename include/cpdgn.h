@@ -75,7 +75,9 @@ enum cp_code {
 /* core-system solver of cp_dgn_solve / cp_dgn_step */
 enum cp_core_mode {
   CP_CORE_F64 = 0,    /* float64 Cholesky of the core system */
-  CP_CORE_MIXED = 1   /* float32 Gauss-Jordan inverse + float64 iterative refinement;
+  CP_CORE_MIXED = 1   /* float32 Gauss-Jordan inverse + float64 iterative refinement
+                         (stops at 1e-15 ||b|| for a float64 tensor, 1e-12 ||b||
+                         for a float32 / bfloat16 one, or on stagnation);
                          a trial whose refinement does not reach 1e-14 ||b|| for a
                          float64 tensor, 1e-8 ||b|| for a float32 / bfloat16 one
                          (an ill-conditioned core) is solved by the float64

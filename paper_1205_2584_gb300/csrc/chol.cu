@@ -8,14 +8,14 @@
 // the number of launches small:
 //
 //  k_chol64 (one persistent launch, one CTA per SM, blocked right-looking
-//  with 32-wide panels).  Per panel k:
-//    phase A  every CTA factors the 32 x 32 diagonal tile in shared memory
-//             (the whole CTA, see factor_tile; redundant across CTAs, so no
-//             barrier separates it from the panel) and solves its share of
-//             the panel's rows X <- X L_kk^{-T} (one warp per row, lane =
-//             column); after the barrier CTA 0 stores L_kk;
+//  with 32-wide panels and a one-tile lookahead).  Per panel k:
+//    phase A  every CTA solves its share of the panel's rows
+//             X <- X L_kk^{-T} (one warp per row, lane = column) with the
+//             stored factor L_kk of the diagonal tile;
 //    phase B  the trailing update A_ij -= L_ik L_jk^T over 32 x 32 tiles of
-//             the lower triangle, tiles dealt round-robin to the CTAs;
+//             the lower triangle: CTA 0 updates the next diagonal tile and
+//             factors it (the whole CTA, see factor_tile), storing L_{k+1,k+1},
+//             while the other tiles are dealt round-robin to the other CTAs;
 //  separated by grid barriers (an arrival counter and a generation word in
 //  the workspace, every wait bounded).  Finally each diagonal tile's inverse
 //  L_cc^{-1} is written to `dinv` for the solves.
@@ -199,58 +199,78 @@ __device__ int factor_tile(double (*D)[CB + 1], int kb, double* rinv) {
   return (bad > 0 && bad <= kb) ? bad : 0;
 }
 
+// CTA 0 factors the diagonal tile kk of A (lower part, already fully
+// updated) in shared memory and stores L_kk in its place, 1 / L_jj into the
+// diagonal of dinv's tile kk and a bad pivot into *info.
+__device__ void factor_store(double* A, int64_t n, int kk, double* dinv, int* info, double (*D)[CB + 1],
+                             double* rinv) {
+  const int64_t k0 = int64_t(kk) * CB;
+  const int kb = int((n - k0) < CB ? (n - k0) : CB);
+  for (int e = threadIdx.x; e < CB * CB; e += CT) {
+    const int i = e % CB, j = e / CB;
+    D[i][j] = (i < kb && j <= i) ? A[(k0 + i) + n * (k0 + j)] : 0.0;
+  }
+  __syncthreads();
+  const int bad = factor_tile(D, kb, rinv);
+  if (threadIdx.x == 0 && bad && info) atomicCAS(info, 0, int(k0) + bad);
+  for (int e = threadIdx.x; e < kb * kb; e += CT) {
+    const int i = e % kb, j = e / kb;
+    if (j <= i) A[(k0 + i) + n * (k0 + j)] = D[i][j];
+  }
+  if (threadIdx.x < CB) dinv[int64_t(kk) * CB * CB + threadIdx.x * (CB + 1)] = rinv[threadIdx.x];
+}
+
+// Lookahead: the diagonal tile of panel k + 1 is the first tile of panel k's
+// trailing update; CTA 0 updates it, factors it and stores L_{k+1,k+1} while
+// the other CTAs update the rest of the trailing matrix, so the diagonal
+// factorisation (about 17 us) leaves the critical path whenever the rest of
+// the update takes longer.  Panel k's rows below the diagonal are then solved
+// by every CTA from the stored L_kk.
 __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* dinv, int* info, CholSync* sy,
                                                int* tmo, const int* skip) {
   if (skip && *skip) return;
   __shared__ double D[CB][CB + 1];
   __shared__ double rinv[CB];
   __shared__ double Pi[CB][CB + 1], Pj[CB][CB + 1];
-  __shared__ int s_bad;
   const unsigned G = gridDim.x;
   const int cta = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nb = int((n + CB - 1) / CB);
   unsigned epoch = 0;
+  if (cta == 0) factor_store(A, n, 0, dinv, info, D, rinv);
+  if (!grid_barrier(sy, G, epoch, info, n, tmo)) return;
   for (int k = 0; k < nb; ++k) {
     const int64_t k0 = int64_t(k) * CB;
     const int kb = int((n - k0) < CB ? (n - k0) : CB);
-    // ---- phase A: diagonal tile and panel solve ----
-    for (int e = tid; e < CB * CB; e += CT) {
-      const int i = e % CB, j = e / CB;
-      D[i][j] = (i < kb && j <= i) ? A[(k0 + i) + n * (k0 + j)] : 0.0;
-    }
-    __syncthreads();
-    {
-      const int bad = factor_tile(D, kb, rinv);
-      if (tid == 0) s_bad = bad;
-    }
-    __syncthreads();
-    for (int64_t r = k0 + kb + int64_t(cta) * 8 + warp; r < n; r += int64_t(G) * 8) {
-      double x = lane < kb ? A[r + n * (k0 + lane)] : 0.0;
+    // ---- phase A: panel solve X <- X L_kk^{-T} with the stored L_kk ----
+    if (k0 + kb < n) {
+      for (int e = tid; e < CB * CB; e += CT) {
+        const int i = e % CB, j = e / CB;
+        D[i][j] = (i < kb && j <= i) ? A[(k0 + i) + n * (k0 + j)] : 0.0;
+      }
+      if (tid < CB) rinv[tid] = tid < kb ? dinv[int64_t(k) * CB * CB + tid * (CB + 1)] : 0.0;
+      __syncthreads();
+      for (int64_t r = k0 + kb + int64_t(cta) * 8 + warp; r < n; r += int64_t(G) * 8) {
+        double x = lane < kb ? A[r + n * (k0 + lane)] : 0.0;
 #pragma unroll 8
-      for (int j = 0; j < kb; ++j) {
-        const double xj = __shfl_sync(0xffffffffu, x, j) * rinv[j];
-        if (lane == j) x = xj;
-        else if (lane > j) x = fma(-xj, D[lane][j], x);
+        for (int j = 0; j < kb; ++j) {
+          const double xj = __shfl_sync(0xffffffffu, x, j) * rinv[j];
+          if (lane == j) x = xj;
+          else if (lane > j) x = fma(-xj, D[lane][j], x);
+        }
+        if (lane < kb) A[r + n * (k0 + lane)] = x;
       }
-      if (lane < kb) A[r + n * (k0 + lane)] = x;
-    }
-    // every CTA has read tile (k, k) of A; CTA 0 may now store L_kk there
-    if (!grid_barrier(sy, G, epoch, info, n, tmo)) return;
-    if (cta == 0) {
-      if (tid == 0 && s_bad && info) atomicCAS(info, 0, int(k0) + s_bad);
-      for (int e = tid; e < kb * kb; e += CT) {
-        const int i = e % kb, j = e / kb;
-        if (j <= i) A[(k0 + i) + n * (k0 + j)] = D[i][j];
-      }
-      // 1 / L_jj: the diagonal of L_kk^{-1}, read by the inverse phase below
-      if (tid < CB) dinv[int64_t(k) * CB * CB + tid * (CB + 1)] = rinv[tid];
     }
     if (k + 1 == nb) break;
+    if (!grid_barrier(sy, G, epoch, info, n, tmo)) return;
     // ---- phase B: trailing update of the lower triangle ----
+    // tile e = 0 is (k + 1, k + 1): CTA 0 alone, then its factorisation;
+    // tiles e >= 1 go to CTAs 1 .. G - 1 (to CTA 0 as well when G == 1)
     const int t = nb - k - 1;
     const int64_t T = int64_t(t) * (t + 1) / 2;
     const int tx = tid & 15, ty = tid >> 4;
-    for (int64_t e = cta; e < T; e += G) {
+    const int64_t e0 = (G == 1) ? 0 : (cta == 0 ? 0 : cta);
+    const int64_t es = (G == 1) ? 1 : (cta == 0 ? T : int64_t(G) - 1);
+    for (int64_t e = e0; e < T; e += es) {
       int ti = int((sqrt(8.0 * double(e) + 1.0) - 1.0) * 0.5);
       while (int64_t(ti + 1) * (ti + 2) / 2 <= e) ++ti;
       while (int64_t(ti) * (ti + 1) / 2 > e) --ti;
@@ -279,11 +299,12 @@ __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* din
           if (r < n && c < n && r >= c) A[r + n * c] -= acc[u][v];
         }
       __syncthreads();
+      if (e == 0) factor_store(A, n, k + 1, dinv, info, D, rinv);   // CTA 0: L_{k+1,k+1}
     }
     if (!grid_barrier(sy, G, epoch, info, n, tmo)) return;
   }
-  // the last diagonal tile, stored by CTA 0 after the last barrier, is read below
-  if (!grid_barrier(sy, G, epoch, info, n, tmo)) return;
+  // every L_kk and 1 / L_jj was stored, and every read of them in a panel
+  // solve finished, before the last barrier of the loop
   // ---- inverses of the diagonal tiles: warps 0-2 of each CTA, one tile each ----
   if (warp < 3) {
     double (*Lt)[CB + 1] = warp == 0 ? D : (warp == 1 ? Pi : Pj);

@@ -77,19 +77,6 @@ __device__ __forceinline__ void load_cols(const float* A, int64_t n, int64_t r0,
   }
 }
 
-// S[r][c] = A(r0 + r, c0 + c) for r, c < 64: a right operand stored row by
-// row.  Global reads are coalesced along r.  NT threads.
-template <int NT>
-__device__ __forceinline__ void load_rows(const float* A, int64_t n, int64_t r0, int64_t c0, float (*S)[GJP]) {
-#pragma unroll
-  for (int q = 0; q < GJB * GJB / NT; ++q) {
-    const int e = int(threadIdx.x) + q * NT;
-    const int r = e % GJB, c = e / GJB;
-    const int64_t gr = r0 + r, gc = c0 + c;
-    S[r][c] = (gr < n && gc < n) ? A[gr + n * gc] : 0.f;
-  }
-}
-
 // the thread's 4 x 8 block of the 64 x 64 tile at (r0, c0); entries outside n x n read as 0
 __device__ __forceinline__ void load_block(const float* A, int64_t n, int64_t r0, int64_t c0, float (&x)[4][8]) {
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
@@ -137,22 +124,6 @@ __device__ __forceinline__ void zero_block(float (&x)[4][8]) {
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 8; ++v) x[u][v] = 0.f;
-}
-
-// x += L R with L = Lc (64 x 64, columns) and R = Rr (64 x 64, rows).
-__device__ __forceinline__ void tile_fma(const float (*Lc)[GJP], const float (*Rr)[GJP], float (&x)[4][8]) {
-  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
-#pragma unroll 8
-  for (int l = 0; l < GJB; ++l) {
-    const float4 a = *reinterpret_cast<const float4*>(&Lc[l][4 * bi]);
-    const float4 b0 = *reinterpret_cast<const float4*>(&Rr[l][8 * bj]);
-    const float4 b1 = *reinterpret_cast<const float4*>(&Rr[l][8 * bj + 4]);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 8; ++v) x[u][v] = fmaf(av[u], bv[v], x[u][v]);
-  }
 }
 
 // ---- half-tile kernels (64 threads, 8 x 4 entries per thread) ----
@@ -633,41 +604,98 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot(const T* A, T* D, int64_t n, i
   pivot_store(x, n, k, kb, Pinv, D, info, prow, pcol, &bad);
 }
 
+// x += SGN L R with L = Lc (64 x 64, stored by columns: Lc[l][r] = L(r, l))
+// and R = Rc (64 x 64, stored by columns: Rc[c][l] = R(l, c)), four inner
+// steps per iteration: four float4 of L and eight float4 of R (two distinct
+// addresses per warp, broadcast) for 128 multiply-adds.
+template <int SGN>
+__device__ __forceinline__ void tile_fma_cc(const float (*Lc)[GJP], const float (*Rc)[GJP], float (&x)[4][8]) {
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+#pragma unroll 2
+  for (int l = 0; l < GJB; l += 4) {
+    float a[4][4], b[8][4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const float4 t = *reinterpret_cast<const float4*>(&Lc[l + w][4 * bi]);
+      a[w][0] = SGN * t.x;
+      a[w][1] = SGN * t.y;
+      a[w][2] = SGN * t.z;
+      a[w][3] = SGN * t.w;
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const float4 t = *reinterpret_cast<const float4*>(&Rc[8 * bj + v][l]);
+      b[v][0] = t.x;
+      b[v][1] = t.y;
+      b[v][2] = t.z;
+      b[v][3] = t.w;
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) x[u][v] = fmaf(a[w][u], b[v][w], x[u][v]);
+  }
+}
+
+// S[c][r] = A(r0 + r, c0 + c) for r, c < 64 by cp.async, 16 bytes (four rows
+// of one column) per copy, zero outside n x n.  Needs n % 4 == 0 (then every
+// source address is 16-byte aligned: r0 and r are multiples of 4).  NT threads.
+template <int NT>
+__device__ __forceinline__ void copy_cols_async(const float* A, int64_t n, int64_t r0, int64_t c0, float (*S)[GJP]) {
+#pragma unroll
+  for (int q = 0; q < GJB * GJB / 4 / NT; ++q) {
+    const int e = int(threadIdx.x) + q * NT;
+    const int r = 4 * (e % 16), c = e / 16;
+    const int64_t gr = r0 + r, gc = c0 + c;
+    const bool in = gr < n && gc < n;
+    cp_async16(&S[c][r], in ? A + gr + n * gc : A, in);
+  }
+}
+
 // Pivot of sweep k + 1 during sweep k, from sweep k's input A and pivot
 // inverse Pinv alone: X = A[k+1,k+1] - A[k+1,k] (P^{-1} A[k,k+1]), inverted;
 // X^{-1} goes to Pinv_next and into A's tile (k+1, k+1), which sweep k + 1
-// writes into and which no kernel of sweep k reads.  All three tiles of A are
-// fetched before the first product.  Launched with kPivotReserve bytes of
-// dynamic shared memory (unused: it keeps the tile CTAs of the concurrent
-// sweep off this SM).
-template <typename T>
+// writes into and which no kernel of sweep k reads.  The three operand tiles
+// are fetched at once (ASYNC, n % 4 == 0: cp.async, 16 bytes a copy; else
+// scalar loads), all stored by columns, before the first product.  Launched
+// with kPivotReserve bytes of dynamic shared memory (unused: it keeps the
+// tile CTAs of the concurrent sweep off this SM).
+template <typename T, bool ASYNC>
 __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, const T* Pinv, T* Pinv_next,
                                                        int* info, const int* skip) {
   pdl_enter();
   if (skip && *skip) return;
-  __shared__ __align__(16) float Ls[GJB][GJP], Rs[GJB][GJP], L2s[GJB][GJP];
+  __shared__ __align__(16) float Ls[GJB][GJP], Rc[GJB][GJP], L2s[GJB][GJP];
   __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
   __shared__ int bad;
   const int k1 = k + 1;
   const int kb = int((n - int64_t(k1) * GJB) < GJB ? (n - int64_t(k1) * GJB) : GJB);
   const int64_t o = int64_t(k) * GJB, o1 = int64_t(k1) * GJB;
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
-  load_cols<GJT>(Pinv, GJB, 0, 0, Ls, 1.f);
-  load_rows<GJT>(A, n, o, o1, Rs);                   // A[k, k+1]
-  load_cols<GJT>(A, n, o1, o, L2s, -1.f);            // -A[k+1, k]
+  if (ASYNC) {
+    copy_cols_async<GJT>(Pinv, GJB, 0, 0, Ls);       // P^{-1}
+    copy_cols_async<GJT>(A, n, o, o1, Rc);           // A[k, k+1]
+    copy_cols_async<GJT>(A, n, o1, o, L2s);          // A[k+1, k]
+    cp_async_commit();
+  } else {
+    load_cols<GJT>(Pinv, GJB, 0, 0, Ls, 1.f);
+    load_cols<GJT>(A, n, o, o1, Rc, 1.f);
+    load_cols<GJT>(A, n, o1, o, L2s, 1.f);
+  }
   float x[4][8], t[4][8];
   load_block(A, n, o1, o1, x);                       // A[k+1, k+1]
   zero_block(t);
+  if (ASYNC) cp_async_wait<0>();
   __syncthreads();
-  tile_fma(Ls, Rs, t);                               // t = P^{-1} A[k, k+1]
+  tile_fma_cc<1>(Ls, Rc, t);                         // t = P^{-1} A[k, k+1]
   __syncthreads();
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    *reinterpret_cast<float4*>(&Rs[4 * bi + u][8 * bj]) = make_float4(t[u][0], t[u][1], t[u][2], t[u][3]);
-    *reinterpret_cast<float4*>(&Rs[4 * bi + u][8 * bj + 4]) = make_float4(t[u][4], t[u][5], t[u][6], t[u][7]);
-  }
+  for (int v = 0; v < 8; ++v)                        // Rc <- t, by columns
+    *reinterpret_cast<float4*>(&Rc[8 * bj + v][4 * bi]) = make_float4(t[0][v], t[1][v], t[2][v], t[3][v]);
   __syncthreads();
-  tile_fma(L2s, Rs, x);
+  tile_fma_cc<-1>(L2s, Rc, x);                       // x = A[k+1,k+1] - A[k+1,k] t
   pad_identity(x, kb);
   pivot_store(x, n, k1, kb, Pinv_next, A, info, prow, pcol, &bad);
 }
@@ -699,8 +727,10 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 template <typename T>
 int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const int* skip, cudaStream_t s,
               cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result) {
-  if (side && cudaFuncSetAttribute(k_gj_pivot_next<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kPivotReserve) != cudaSuccess)
+  if (side && (cudaFuncSetAttribute(k_gj_pivot_next<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kPivotReserve) != cudaSuccess ||
+               cudaFuncSetAttribute(k_gj_pivot_next<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kPivotReserve) != cudaSuccess))
     return CP_ECUDA;
   const int nt = int((n + GJB - 1) / GJB);
   T* src = A;
@@ -734,7 +764,8 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
       if (next && side) {
         if (cudaEventRecord(ev_fork, s) != cudaSuccess) return CP_ECUDA;
         if (cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return CP_ECUDA;
-        k_gj_pivot_next<T><<<1, GJT, kPivotReserve, side>>>(src, n, k, pk, pn, info, skip);
+        if (n % 4 == 0) k_gj_pivot_next<T, true><<<1, GJT, kPivotReserve, side>>>(src, n, k, pk, pn, info, skip);
+        else k_gj_pivot_next<T, false><<<1, GJT, kPivotReserve, side>>>(src, n, k, pk, pn, info, skip);
         if (cudaEventRecord(ev_join, side) != cudaSuccess) return CP_ECUDA;
       }
       if (n % 4 == 0) {

@@ -413,8 +413,8 @@ __global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double
 // CP_CORE_F64: L64 holds the float64 Cholesky factor, two triangular solves.
 // CP_CORE_MIXED: X32 holds the float32 inverse of the core; y = X b, then up
 // to refine_iters sweeps y += X (b - y - S^T K S y) with the float64
-// operator, stopping once ||b - core y|| <= 1e-15 ||b|| or the residual stops
-// shrinking (kernels of later sweeps return at once; the graph is fixed).
+// operator, stopping once ||b - core y|| <= 1e-15 ||b|| (1e-12 ||b|| for
+// float32 and bfloat16 tensors) or the residual stops shrinking (kernels of later sweeps return at once; the graph is fixed).
 // b = S^T (K w), ||b||^2 (nrm[0]) and K w, the right-hand side of the core
 // system; it needs the per-mode preparation only, not the core.
 static int core_rhs(const Dims& d, const Bufs& B, const int* skip, cudaStream_t s) {
@@ -464,12 +464,17 @@ static int solve_core(const Dims& d, const Bufs& B, double* core64, const float*
   } else {
     int* rdone = B.info + IN_RDONE;
     const int K = refine_iters < kMaxRefine ? refine_iters : kMaxRefine;
+    // refinement target: 1e-15 ||b|| for a float64 tensor; 1e-12 ||b|| for
+    // float32 and bfloat16 tensors, whose gradient blocks carry float32
+    // rounding (relative 1e-7 and more), so that a tighter solve changes the
+    // step by less than its own rounding error while costing 1-2 more sweeps
+    const double rtol2 = (d.y_dtype == CP_F64) ? 1e-30 : 1e-24;
     CP_CUDA(cudaMemsetAsync(B.y, 0, n * sizeof(double), s));
     CP_TRY(launch_gemv_acc(X32, n, B.b, B.y, nullptr, nullptr, nullptr, nullptr, 0.0, skip, s));
     for (int it = 1; it <= K; ++it) {
       CP_TRY(launch_apply_S(d, B.LC, B.U, B.y, B.Z, rdone, s));
       CP_TRY(launch_apply_ST(d, B.LC, B.U, B.Gnm, B.Z, 1, B.b, B.y, B.res, nullptr, nrm + it, rdone, s));
-      CP_TRY(launch_gemv_acc(X32, n, B.res, B.y, nrm, nrm + it, it > 1 ? nrm + it - 1 : nullptr, rdone, 1e-30,
+      CP_TRY(launch_gemv_acc(X32, n, B.res, B.y, nrm, nrm + it, it > 1 ? nrm + it - 1 : nullptr, rdone, rtol2,
                              rdone, s));
     }
     if (core64) {
