@@ -29,9 +29,12 @@
 // so each k-step reads two float4 of the left operand and one of the right
 // operand for 32 multiply-adds; eight consecutive lanes read eight
 // consecutive float4, free of shared-memory bank conflicts.
+#include <cuda_bf16.h>
+
 #include <mutex>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace cpdgn {
 
@@ -429,6 +432,201 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
   h_store_block(acc, B, n, r0, c0);
 }
 
+// ---- the rank-64 update on the tensor cores (tcgen05) ----
+//
+// One CTA (256 threads) per 128 x 128 output tile of
+//     B[i, j] = (j in block k ? 0 : A[i, j]) - sum_l A[i, 64 k + l] R[l, j],
+// R = row block k of B as the row panel left it (P^{-1} A[k, j], and P^{-1}
+// itself in tile (k, k), where the pivot kernel stored it).  Rows of block k
+// (the row panel's output) and, with skip_pivot, tile (k + 1, k + 1) (the
+// next-pivot kernel's) are not written.  Each thread splits half a row of the
+// column-panel slice (128 x 64) and half a column of the row-panel slice
+// (64 x 128) into three bfloat16 pieces (x = x0 + x1 + x2, 24 significant
+// bits) in shared memory, in the no-swizzle K-major layout of 8 x 16-byte
+// core matrices (8-row groups 1024 bytes apart); one thread issues the six
+// piece products down to 2^-16 relative (x0 y0, x0 y1, x1 y0, x1 y1, x0 y2,
+// x2 y0: float32-level products), 4 MMAs of K = 16 each, accumulating in
+// 128 TMEM columns; each warp reads 32 lanes (rows) x 64 columns back, loads
+// the 32 values of A of a column group before it stores any of B, and
+// writes B coalesced along the column.  The wait for the MMAs is bounded: when it
+// runs out the tile is not written, *info is set to n + 1 (the inverse is
+// then rejected like one with a bad pivot), the timeout counter grows, and
+// the CTA waits once more (bounded) before it frees its tensor memory.
+constexpr int kUtM = 128;                          // rows (i) per tile
+constexpr int kUtN = 128;                          // columns (j) per tile
+constexpr int kUtPiece = 128 * GJB * 2;            // one bfloat16 piece of a 128 x 64 operand: 16 KB
+constexpr int kUtSmem = 6 * kUtPiece;              // three pieces of each operand
+constexpr int64_t kUtMinN = 1024;                  // smallest core inverted with tensor-core updates (measured: 768 and 900 are faster on the SIMT update)
+int tc_timeout_counter(int** out);
+
+__device__ __forceinline__ uint32_t ut_off(int row, int col) {
+  return uint32_t((row >> 3) * 1024 + (col >> 3) * 128 + (row & 7) * 16 + (col & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t ut_pack(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return uint32_t(__bfloat16_as_ushort(lo)) | (uint32_t(__bfloat16_as_ushort(hi)) << 16);
+}
+
+// the three bfloat16 pieces of 32 values of operand row `row`, inner index
+// l0 .. l0 + 31
+__device__ __forceinline__ void ut_store_half(unsigned char* base, int row, int l0, const float (&v)[32]) {
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      __nv_bfloat16 x0[2], x1[2], x2[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float x = v[8 * g + 2 * h + q];
+        x0[q] = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(x0[q]);
+        x1[q] = __float2bfloat16_rn(r1);
+        x2[q] = __float2bfloat16_rn(r1 - __bfloat162float(x1[q]));
+      }
+      w0[h] = ut_pack(x0[0], x0[1]);
+      w1[h] = ut_pack(x1[0], x1[1]);
+      w2[h] = ut_pack(x2[0], x2[1]);
+    }
+    const uint32_t o = ut_off(row, l0 + 8 * g);
+    *reinterpret_cast<uint4*>(base + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    *reinterpret_cast<uint4*>(base + kUtPiece + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4*>(base + 2 * kUtPiece + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  }
+}
+
+// Shared memory of k_gj_update_tc: the six bfloat16 pieces, then a float32
+// staging area that first holds the two operand slices as copied (column
+// panel [l][row], row panel [j][l] with rows padded to GJP floats so that the
+// split reads no bank twice) and then the 128 x 128 tile of A to subtract from.
+constexpr int kUtStage = (GJB * kUtM + kUtN * GJP) * 4;                  // 66.8 KB >= 128 x 128 x 4
+constexpr int kUtSmemAll = kUtSmem + kUtStage;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_update_tc(const T* __restrict__ A, T* __restrict__ B, int64_t n, int k,
+                                                      int skip_pivot, const int* skip, int* info, int* tmo) {
+  pdl_enter();
+  if (skip && *skip) return;
+  extern __shared__ __align__(1024) unsigned char ut_smem[];
+  unsigned char* apc = ut_smem;                    // column-panel slice pieces, rows = i
+  unsigned char* rpc = ut_smem + 3 * kUtPiece;     // row-panel slice pieces, rows = j
+  float (*sa)[kUtM] = reinterpret_cast<float (*)[kUtM]>(ut_smem + kUtSmem);              // [l][row]
+  float (*sr)[GJP] = reinterpret_cast<float (*)[GJP]>(ut_smem + kUtSmem + GJB * kUtM * 4); // [j][l]
+  float (*si)[kUtM] = reinterpret_cast<float (*)[kUtM]>(ut_smem + kUtSmem);              // [c][row], later
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tbase_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t i0 = int64_t(blockIdx.x) * kUtM, j0 = int64_t(blockIdx.y) * kUtN;
+  const int64_t ko = int64_t(k) * GJB;
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase_s, 128);
+    tc::tmem_relinquish();
+  }
+  // both operand slices in flight at once (16 bytes a copy; n % 4 == 0, so a
+  // copy is wholly inside or wholly outside the matrix)
+#pragma unroll
+  for (int q = 0; q < GJB * kUtM / 4 / 256; ++q) {           // A(i0 + r, ko + l)
+    const int e = tid + 256 * q, l = e / 32, r = 4 * (e % 32);
+    const bool in = i0 + r < n && ko + l < n;
+    cp_async16(&sa[l][r], in ? A + (i0 + r) + n * (ko + l) : A, in);
+  }
+#pragma unroll
+  for (int q = 0; q < kUtN * GJB / 4 / 256; ++q) {           // R(l, j0 + j) = B(ko + l, j0 + j)
+    const int e = tid + 256 * q, j = e / 16, l = 4 * (e % 16);
+    const bool in = j0 + j < n && ko + l < n;
+    cp_async16(&sr[j][l], in ? B + (ko + l) + n * (j0 + j) : B, in);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  {
+    const int row = tid & 127, l0 = 32 * (tid >> 7);          // one operand row, half of the inner index
+    float v[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) v[l] = sa[l0 + l][row];
+    ut_store_half(apc, row, l0, v);
+#pragma unroll
+    for (int l = 0; l < 32; l += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(&sr[row][l0 + l]);
+      v[l] = t.x;
+      v[l + 1] = t.y;
+      v[l + 2] = t.z;
+      v[l + 3] = t.w;
+    }
+    ut_store_half(rpc, row, l0, v);
+  }
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tb = tbase_s;
+  if (tid == 0) {
+    const uint32_t id = tc::idesc_bf16(kUtM, kUtN, false, false);
+    const uint32_t sa_ = tc::smem_u32(apc), sr_ = tc::smem_u32(rpc);
+    constexpr int pa[6] = {0, 0, 1, 1, 0, 2}, pr[6] = {0, 1, 0, 1, 2, 0};
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int ks = 0; ks < GJB / 16; ++ks)
+        tc::mma_bf16(tb, tc::sdesc(sa_ + pa[c] * kUtPiece + ks * 256, 128, 1024),
+                     tc::sdesc(sr_ + pr[c] * kUtPiece + ks * 256, 128, 1024), id, (c | ks) ? 1u : 0u);
+    tc::mma_commit(&bar);
+  }
+  __syncwarp();
+  // the tile of A to subtract from, into the staging area, while the MMAs run
+#pragma unroll
+  for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {
+    const int e = tid + 256 * q, c = e / 32, r = 4 * (e % 32);
+    const bool in = i0 + r < n && j0 + c < n;
+    cp_async16(&si[c][r], in ? A + (i0 + r) + n * (j0 + c) : A, in);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  const bool ok = __syncthreads_and(tc::mbar_wait(&bar, 0) ? 1 : 0) != 0;
+  if (ok) {
+    tc::tc_fence_after();
+    // warp w: TMEM lanes (rows) 32 (w % 4) .., columns 64 (w / 4) .. + 63;
+    // the result replaces the staged tile in shared memory (lanes = rows:
+    // no bank is read twice), then the CTA stores it along the columns
+    const int qr = warp & 3, cbase = 64 * (warp >> 2), r = 32 * qr + lane;
+#pragma unroll 1
+    for (int c0 = cbase; c0 < cbase + 64; c0 += 32) {
+      float d[32];
+      tc::tmem_ld32(tb + (uint32_t(32 * qr) << 16) + uint32_t(c0), d);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int64_t j = j0 + c0 + c;
+        si[c0 + c][r] = ((j / GJB == k) ? 0.f : si[c0 + c][r]) - d[c];
+      }
+    }
+  }
+  __syncthreads();
+  if (ok) {
+    // four rows per copy: a 64-row block boundary never splits one
+#pragma unroll 4
+    for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {
+      const int e = tid + 256 * q, c = e / 32, rr = 4 * (e % 32);
+      const int64_t i = i0 + rr, j = j0 + c;
+      const int64_t bi = i / GJB, bj = j / GJB;
+      if (i < n && j < n && bi != k && !(skip_pivot && bi == k + 1 && bj == k + 1))
+        *reinterpret_cast<float4*>(B + i + n * j) = *reinterpret_cast<const float4*>(&si[c][rr]);
+    }
+  } else {
+    if (tid == 0) {
+      if (tmo) atomicAdd(tmo, 1);
+      if (info) atomicCAS(info, 0, int(n + 1));
+    }
+    tc::mbar_wait(&bar, 0);                        // the MMAs may still run: bounded drain
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tb, 128);
+}
+
 // The first kb0 tiles of the core lie inside its leading identity block
 // (the core's diagonal R^2 x R^2 blocks are I).  Eliminating them at once
 // (pivot I of size kb0 * GJB) maps A -> B as
@@ -702,10 +900,10 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, c
 
 // Launch with the programmatic-serialisation attribute (see pdl_enter).
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s,
                               Args... args) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
+  cfg.gridDim = grid;
   cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -726,7 +924,17 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 // graph-capturable).
 template <typename T>
 int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const int* skip, cudaStream_t s,
-              cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result) {
+              cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result, int tc_mode) {
+  // the rank-64 updates on the tensor cores from n = kUtMinN (tc_mode < 0),
+  // or as tc_mode says (0: SIMT, 1: tensor cores)
+  const bool use_tc = n % 4 == 0 && (tc_mode < 0 ? (n >= kUtMinN) : (tc_mode != 0));
+  int* tmo = nullptr;
+  if (use_tc) {
+    if (tc_timeout_counter(&tmo) != CP_OK) return CP_ECUDA;
+    if (cudaFuncSetAttribute(k_gj_update_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUtSmemAll) !=
+        cudaSuccess)
+      return CP_ECUDA;
+  }
   if (side && (cudaFuncSetAttribute(k_gj_pivot_next<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kPivotReserve) != cudaSuccess ||
                cudaFuncSetAttribute(k_gj_pivot_next<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -768,7 +976,17 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
         else k_gj_pivot_next<T, false><<<1, GJT, kPivotReserve, side>>>(src, n, k, pk, pn, info, skip);
         if (cudaEventRecord(ev_join, side) != cudaSuccess) return CP_ECUDA;
       }
-      if (n % 4 == 0) {
+      if (use_tc) {
+        const unsigned mt = unsigned((n + kUtM - 1) / kUtM), ntc = unsigned((n + kUtN - 1) / kUtN);
+        if (n % 4 == 0 ? launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk,
+                                    skip) != cudaSuccess
+                       : launch_pdl(k_gj_rowpanel<T, false>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk,
+                                    skip) != cudaSuccess)
+          return CP_ECUDA;
+        if (launch_pdl(k_gj_update_tc<T>, dim3(mt, ntc), 256, kUtSmemAll, s, src, dst, n, k, (next && side) ? 1 : 0,
+                       skip, info, tmo) != cudaSuccess)
+          return CP_ECUDA;
+      } else if (n % 4 == 0) {
         if (launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk, skip) !=
                 cudaSuccess ||
             launch_pdl(k_gj_update<T, true>, (nt - 1) * nt * 2, GJTH, kTileSmem, s, src, dst, n, k, pk,
@@ -796,7 +1014,7 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 template int gj_invert<float>(float*, float*, float*, int64_t, int64_t, int*, const int*, cudaStream_t,
-                               cudaStream_t, cudaEvent_t, cudaEvent_t, float**);
+                               cudaStream_t, cudaEvent_t, cudaEvent_t, float**, int);
 
 // y += X r  (X n x n float32 column-major, r and y float64).  CTA = (row block,
 // column slice); partial sums of the slice are added with atomics.  When b2
@@ -871,7 +1089,7 @@ extern "C" int cp_spd_invert_f32(int64_t n, int64_t ident, float* A, float* work
   if (info && cudaMemsetAsync(info, 0, sizeof(int), s) != cudaSuccess) return CP_ECUDA;
   float* res = nullptr;
   const int rc = cpdgn::gj_invert<float>(A, work, pinv, n, ident, info, nullptr, s, g_inv_side, g_inv_fork,
-                                         g_inv_join, &res);
+                                         g_inv_join, &res, -1);
   if (rc != CP_OK) return rc;
   *in_work = (res == work) ? 1 : 0;
   return CP_OK;

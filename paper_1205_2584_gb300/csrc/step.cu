@@ -52,7 +52,7 @@ int chol64_solve(const double* L, const double* dinv, int64_t n, const double* b
                  void* sync, int* info, int* tmo, const int* skip, cudaStream_t s);
 template <typename T>
 int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const int* skip, cudaStream_t s,
-              cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result);
+              cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result, int tc_mode = -1);
 int tc_timeout_counter(int** out);
 int launch_gemv_acc(const float* X, int64_t n, const double* r, double* y, const double* b2, const double* r2,
                     const double* r2prev, int* done, double tol2, const int* skip, cudaStream_t s);
