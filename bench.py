@@ -655,6 +655,7 @@ def _run_ours(args, rank, world, local):
 
         out["config1"] = bench_config1(cp, O, torch, seed)
         out["config3"] = bench_config3(cp, O, torch, seed, flush)
+        out["next_rows"] = bench_next_rows(cp, O, torch, seed, prob, Y32)
         if not args.no_batch:
             out["batched"] = bench_batched(seed)
         if args.serve_seconds > 0:
@@ -822,6 +823,124 @@ def bench_config3(cp, O, torch, seed, flush):
     out["final_eps_mixed_vs_f64"] = abs(out["mixed_bf16"]["rel_err"] - out["plain_f64"]["rel_err"]) / \
         out["plain_f64"]["rel_err"]
     out["step_state"] = {"mu": mu0, "kappa_core": core_kappa(O, p.init, mu0)}
+    return out
+
+
+def bench_next_rows(cp, O, torch, seed, prob, Y32):
+    """The later rows of the method, each timed on the device and compared
+    with the float64 oracle on the same inputs:
+      hosvd     cp_hosvd (Algorithm 1 step 1) on the benchmark tensor
+                (200^3, R = 20, float32 values), 30 subspace iterations;
+      theorem4  cp_hinv_blocks + cp_hinv_diag (Theorem 4, Eq. fastblock) at
+                the benchmark's start factors (N R^2 = 1200), mu = 1;
+      sae       cp_sae (Eq. MedSAE: cosines, Hungarian matching) of the true
+                factors against a perturbed, permuted copy, R = 20;
+      complex   cp_cdgn_step (Theorems 5-8) on 70^4, R = 5 complex128 (the
+                paper's complex experiments); the step error on 30^4, R = 5."""
+    from paper_1205_2584_gb300 import synth
+    import numpy as np
+    out = {}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    dims, R = prob.dims, prob.R
+    shape = cp.make_shape(dims, R, "f32")
+    a = torch.empty(R * sum(dims), dtype=torch.float64, device="cuda")
+    ms = timed(lambda: cp.hosvd(shape, Y32, a, iters=30), 5)
+    got = cp.split_factors(a.cpu(), dims, R)
+    Yv = np.asarray(prob.Y, dtype=np.float32).astype(np.float64)
+    ref = O.hosvd_factors(Yv, R)
+    err = max(float(np.max(np.abs(got[n].numpy() - ref[n]))) for n in range(len(dims)))
+    out["hosvd"] = {"workload": f"{dims[0]}^3, R={R}, float32 tensor, 30 subspace iterations", "ms": ms,
+                    "max_abs_err_vs_oracle": err}
+
+    shape64 = cp.make_shape(dims, R, "f64")
+    a0 = cp.factors_to_device(prob.init)
+    mu = 1.0
+    res = {}
+
+    def hb():
+        res["b"] = cp.hinv_blocks(shape64, a0, mu)
+    ms_b = timed(hb, 5)
+    Gt, St, info = res["b"]
+    ms_d = timed(lambda: cp.hinv_diag(shape64, a0, Gt, St), 5)
+    Gt_ref, St_ref = O.hinv_blocks(prob.init, mu)
+    n = len(dims) * R * R
+    St_np = St.cpu().numpy().reshape(n, n, order="F")
+    T = sum(dims)
+    out["theorem4"] = {"workload": f"{dims[0]}^3, R={R} start factors, mu = 1 (N R^2 = {n})",
+                       "blocks_ms": ms_b, "diag_ms": ms_d, "info": int(info.item()),
+                       "St_rel_err_vs_oracle": _rel(St_np, St_ref),
+                       "stored_doubles": len(dims) * R * R + n * n, "full_inverse_doubles": (R * T) ** 2}
+
+    rng = np.random.default_rng(seed + 7)
+    A = [np.asarray(f) for f in prob.true_factors]
+    perm = rng.permutation(R)
+    est = [(f + 0.05 * rng.standard_normal(f.shape))[:, perm] * rng.choice([-1.0, 1.0], R) for f in A]
+    at, ae = cp.factors_to_device(A), cp.factors_to_device(est)
+    res2 = {}
+
+    def sf():
+        res2["s"] = cp.sae(shape64, at, ae)
+    us = 1e3 * timed(sf, 20)
+    a2, pi = res2["s"]
+    a2_ref, pi_ref = O.sae(A, est)
+    out["sae"] = {"workload": f"N=3, R={R}, I_n={dims[0]}: true factors vs a perturbed, permuted copy",
+                  "us_per_call": us, "max_abs_err_vs_oracle": float(np.max(np.abs(a2.cpu().numpy() - a2_ref))),
+                  "permutation_equal": bool(np.array_equal(pi.cpu().numpy(), np.asarray(pi_ref))),
+                  "medsae_db": cp.medsae_db([a2]), "oracle_medsae_db": O.medsae([a2_ref])}
+
+    pc = synth.make_complex_problem(seed + 250, (70, 70, 70, 70), 5, snr_db=30)
+    shc = cp.make_shape(pc.dims, pc.R, "c128")
+    Yc = cp.ctensor_to_device(pc.Y)
+    ac = cp.cfactors_to_device(pc.init)
+    ac0 = ac.clone()
+    st = cp.CState(shc, ac, mu0=-1.0, max_iter=100000, tol=0.0, normalize=True)
+    k, best = 20, float("inf")
+    for _ in range(4):                             # 20 trials from the start factors, the first run a warm-up
+        ac.copy_(ac0)
+        st.init(Yc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            st.step(Yc)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    ms_c = best / k
+    sc = st.status()
+    st.close()
+    del Yc
+    ps = synth.make_complex_problem(seed + 251, (30, 30, 30, 30), 5, snr_db=30)
+    shs = cp.make_shape(ps.dims, ps.R, "c128")
+    Ys = cp.ctensor_to_device(ps.Y)
+    asm = cp.cfactors_to_device(ps.init)
+    mu_s = 0.5
+    st = cp.CState(shs, asm, mu0=mu_s, max_iter=10, normalize=False)
+    st.init(Ys)
+    st.step(Ys)
+    torch.cuda.synchronize()
+    nA = ps.R * sum(ps.dims)
+    d = st.buffer(cp.CState.BUF_DELTA, nA).cpu().numpy()
+    st.close()
+    ref_d = O.cflm_step(ps.Y, ps.init, mu_s)[0]
+    ref_flat = np.concatenate([np.asarray(x).T.reshape(-1) for x in ref_d])
+    out["complex"] = {"workload": "70^4, R=5, complex128, snr 30 (the paper's complex experiments)",
+                      "iters_per_s": 1e3 / ms_c, "ms_per_step": ms_c, "iters": sc["iters"],
+                      "rel_err_after": sc["rel_err"],
+                      "step_rel_err_vs_oracle": float(np.linalg.norm(d - ref_flat) / np.linalg.norm(ref_flat)),
+                      "step_case": "30^4, R=5, mu = 0.5, from the start factors"}
     return out
 
 
