@@ -432,26 +432,35 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
   h_store_block(acc, B, n, r0, c0);
 }
 
-// ---- the rank-64 update on the tensor cores (tcgen05) ----
+// ---- rank-64 k updates on the tensor cores (tcgen05) ----
 //
-// One CTA (256 threads) per 128 x 128 output tile of
-//     B[i, j] = (j in block k ? 0 : A[i, j]) - sum_l A[i, 64 k + l] R[l, j],
-// R = row block k of B as the row panel left it (P^{-1} A[k, j], and P^{-1}
-// itself in tile (k, k), where the pivot kernel stored it).  Rows of block k
-// (the row panel's output) and, with skip_pivot, tile (k + 1, k + 1) (the
-// next-pivot kernel's) are not written.  Each thread splits half a row of the
-// column-panel slice (128 x 64) and half a column of the row-panel slice
-// (64 x 128) into three bfloat16 pieces (x = x0 + x1 + x2, 24 significant
-// bits) in shared memory, in the no-swizzle K-major layout of 8 x 16-byte
-// core matrices (8-row groups 1024 bytes apart); one thread issues the six
-// piece products down to 2^-16 relative (x0 y0, x0 y1, x1 y0, x1 y1, x0 y2,
-// x2 y0: float32-level products), 4 MMAs of K = 16 each, accumulating in
-// 128 TMEM columns; each warp reads 32 lanes (rows) x 64 columns back, loads
-// the 32 values of A of a column group before it stores any of B, and
-// writes B coalesced along the column.  The wait for the MMAs is bounded: when it
-// runs out the tile is not written, *info is set to n + 1 (the inverse is
-// then rejected like one with a bad pivot), the timeout counter grows, and
-// the CTA waits once more (bounded) before it frees its tensor memory.
+// One CTA (256 threads) per 128 x 128 output tile of a rank-(64 nkb) update
+//     B[i, j] = init(i, j) - sum_{l < 64 nkb} A[i, ko + l] R[ko + l, j],
+// in one of two modes:
+//   sweep k (k >= 0, nkb = 1, ko = 64 k, tiles over the whole matrix):
+//     R = row block k of B as the row panel left it (P^{-1} A[k, j], and
+//     P^{-1} itself in tile (k, k), where the pivot kernel stored it);
+//     init = 0 in column block k, else A[i, j]; rows of block k (the row
+//     panel's output) and, with skip_pivot, tile (k + 1, k + 1) (the
+//     next-pivot kernel's) are not written;
+//   identity elimination (k < 0, ko = 0, tiles over [base, n)^2 with
+//     base = 64 nkb): R = A, init = A[i, j] (the trailing part of the
+//     one-launch elimination of the leading identity block).
+// Per K block of 64 the two operand slices (128 x 64 of the column panel,
+// 64 x 128 of the row panel) are copied to a float32 staging area by
+// cp.async; each thread splits half a row of each into three bfloat16
+// pieces (x = x0 + x1 + x2, 24 significant bits) in the no-swizzle K-major
+// layout of 8 x 16-byte core matrices (8-row groups 1024 bytes apart); one
+// thread issues the six piece products down to 2^-16 relative (x0 y0, x0 y1,
+// x1 y0, x1 y1, x0 y2, x2 y0: float32-level products), 4 MMAs of K = 16
+// each, accumulating in 128 TMEM columns, while the next block's slices are
+// copied.  Then the tile of A to subtract from is staged the same way, each
+// warp reads 32 lanes (rows) x 64 columns of the accumulator back into it,
+// and the CTA stores the result along the columns with 16-byte stores.
+// Every wait for the MMAs is bounded: when one runs out the tile is not
+// written, *info is set to n + 1 (the inverse is then rejected like one with
+// a bad pivot), the timeout counter grows, and the CTA waits once more
+// (bounded) before it frees its tensor memory.
 constexpr int kUtM = 128;                          // rows (i) per tile
 constexpr int kUtN = 128;                          // columns (j) per tile
 constexpr int kUtPiece = 128 * GJB * 2;            // one bfloat16 piece of a 128 x 64 operand: 16 KB
@@ -496,15 +505,38 @@ __device__ __forceinline__ void ut_store_half(unsigned char* base, int row, int 
 }
 
 // Shared memory of k_gj_update_tc: the six bfloat16 pieces, then a float32
-// staging area that first holds the two operand slices as copied (column
-// panel [l][row], row panel [j][l] with rows padded to GJP floats so that the
-// split reads no bank twice) and then the 128 x 128 tile of A to subtract from.
+// staging area that holds the two operand slices of a K block as copied
+// (column panel [l][row], row panel [j][l] with rows padded to GJP floats so
+// that the split reads no bank twice) and at the end the 128 x 128 tile of A
+// to subtract from.
 constexpr int kUtStage = (GJB * kUtM + kUtN * GJP) * 4;                  // 66.8 KB >= 128 x 128 x 4
 constexpr int kUtSmemAll = kUtSmem + kUtStage;
 
+// 16-byte copies of K block kb's operand slices into the staging area;
+// n % 4 == 0, so a copy is wholly inside or wholly outside the matrix
 template <typename T>
-__global__ void __launch_bounds__(256) k_gj_update_tc(const T* __restrict__ A, T* __restrict__ B, int64_t n, int k,
-                                                      int skip_pivot, const int* skip, int* info, int* tmo) {
+__device__ __forceinline__ void ut_copy_slices(const T* A, const T* Rs, int64_t n, int64_t i0, int64_t j0,
+                                               int64_t kc, float (*sa)[kUtM], float (*sr)[GJP]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < GJB * kUtM / 4 / 256; ++q) {           // A(i0 + r, kc + l)
+    const int e = tid + 256 * q, l = e / 32, r = 4 * (e % 32);
+    const bool in = i0 + r < n && kc + l < n;
+    cp_async16(&sa[l][r], in ? A + (i0 + r) + n * (kc + l) : A, in);
+  }
+#pragma unroll
+  for (int q = 0; q < kUtN * GJB / 4 / 256; ++q) {           // R(kc + l, j0 + j)
+    const int e = tid + 256 * q, j = e / 16, l = 4 * (e % 16);
+    const bool in = j0 + j < n && kc + l < n;
+    cp_async16(&sr[j][l], in ? Rs + (kc + l) + n * (j0 + j) : Rs, in);
+  }
+  cp_async_commit();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_update_tc(const T* A, T* B, const T* Rs, int64_t n, int64_t base,
+                                                      int64_t ko, int nkb, int k, int skip_pivot, const int* skip,
+                                                      int* info, int* tmo) {
   pdl_enter();
   if (skip && *skip) return;
   extern __shared__ __align__(1024) unsigned char ut_smem[];
@@ -512,12 +544,11 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* __restrict__ A, T
   unsigned char* rpc = ut_smem + 3 * kUtPiece;     // row-panel slice pieces, rows = j
   float (*sa)[kUtM] = reinterpret_cast<float (*)[kUtM]>(ut_smem + kUtSmem);              // [l][row]
   float (*sr)[GJP] = reinterpret_cast<float (*)[GJP]>(ut_smem + kUtSmem + GJB * kUtM * 4); // [j][l]
-  float (*si)[kUtM] = reinterpret_cast<float (*)[kUtM]>(ut_smem + kUtSmem);              // [c][row], later
+  float (*si)[kUtM] = reinterpret_cast<float (*)[kUtM]>(ut_smem + kUtSmem);              // [c][row], at the end
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tbase_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t i0 = int64_t(blockIdx.x) * kUtM, j0 = int64_t(blockIdx.y) * kUtN;
-  const int64_t ko = int64_t(k) * GJB;
+  const int64_t i0 = base + int64_t(blockIdx.x) * kUtM, j0 = base + int64_t(blockIdx.y) * kUtN;
   if (tid == 0) {
     tc::mbar_init(&bar, 1);
     tc::fence_barrier_init();
@@ -526,67 +557,66 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* __restrict__ A, T
     tc::tmem_alloc(&tbase_s, 128);
     tc::tmem_relinquish();
   }
-  // both operand slices in flight at once (16 bytes a copy; n % 4 == 0, so a
-  // copy is wholly inside or wholly outside the matrix)
-#pragma unroll
-  for (int q = 0; q < GJB * kUtM / 4 / 256; ++q) {           // A(i0 + r, ko + l)
-    const int e = tid + 256 * q, l = e / 32, r = 4 * (e % 32);
-    const bool in = i0 + r < n && ko + l < n;
-    cp_async16(&sa[l][r], in ? A + (i0 + r) + n * (ko + l) : A, in);
-  }
-#pragma unroll
-  for (int q = 0; q < kUtN * GJB / 4 / 256; ++q) {           // R(l, j0 + j) = B(ko + l, j0 + j)
-    const int e = tid + 256 * q, j = e / 16, l = 4 * (e % 16);
-    const bool in = j0 + j < n && ko + l < n;
-    cp_async16(&sr[j][l], in ? B + (ko + l) + n * (j0 + j) : B, in);
-  }
-  cp_async_commit();
-  cp_async_wait<0>();
-  __syncthreads();
-  {
-    const int row = tid & 127, l0 = 32 * (tid >> 7);          // one operand row, half of the inner index
-    float v[32];
-#pragma unroll
-    for (int l = 0; l < 32; ++l) v[l] = sa[l0 + l][row];
-    ut_store_half(apc, row, l0, v);
-#pragma unroll
-    for (int l = 0; l < 32; l += 4) {
-      const float4 t = *reinterpret_cast<const float4*>(&sr[row][l0 + l]);
-      v[l] = t.x;
-      v[l + 1] = t.y;
-      v[l + 2] = t.z;
-      v[l + 3] = t.w;
+  ut_copy_slices(A, Rs, n, i0, j0, ko, sa, sr);
+  const uint32_t id = tc::idesc_bf16(kUtM, kUtN, false, false);
+  bool ok = true;
+  int kb = 0;
+  for (; kb < nkb; ++kb) {
+    cp_async_wait<0>();
+    __syncthreads();                               // staging holds block kb
+    if (kb > 0) {                                  // the pieces are free once block kb - 1's MMAs are done
+      ok = __syncthreads_and(tc::mbar_wait(&bar, uint32_t(kb - 1) & 1u) ? 1 : 0) != 0;
+      if (!ok) break;
     }
-    ut_store_half(rpc, row, l0, v);
-  }
-  tc::fence_async_smem();
-  tc::tc_fence_before();
-  __syncthreads();
-  tc::tc_fence_after();
-  const uint32_t tb = tbase_s;
-  if (tid == 0) {
-    const uint32_t id = tc::idesc_bf16(kUtM, kUtN, false, false);
-    const uint32_t sa_ = tc::smem_u32(apc), sr_ = tc::smem_u32(rpc);
-    constexpr int pa[6] = {0, 0, 1, 1, 0, 2}, pr[6] = {0, 1, 0, 1, 2, 0};
+    {
+      const int row = tid & 127, l0 = 32 * (tid >> 7);        // one operand row, half of the inner index
+      float v[32];
 #pragma unroll
-    for (int c = 0; c < 6; ++c)
+      for (int l = 0; l < 32; ++l) v[l] = sa[l0 + l][row];
+      ut_store_half(apc, row, l0, v);
 #pragma unroll
-      for (int ks = 0; ks < GJB / 16; ++ks)
-        tc::mma_bf16(tb, tc::sdesc(sa_ + pa[c] * kUtPiece + ks * 256, 128, 1024),
-                     tc::sdesc(sr_ + pr[c] * kUtPiece + ks * 256, 128, 1024), id, (c | ks) ? 1u : 0u);
-    tc::mma_commit(&bar);
-  }
-  __syncwarp();
-  // the tile of A to subtract from, into the staging area, while the MMAs run
+      for (int l = 0; l < 32; l += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(&sr[row][l0 + l]);
+        v[l] = t.x;
+        v[l + 1] = t.y;
+        v[l + 2] = t.z;
+        v[l + 3] = t.w;
+      }
+      ut_store_half(rpc, row, l0, v);
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (tid == 0) {
+      const uint32_t tb = tbase_s;
+      const uint32_t sa_ = tc::smem_u32(apc), sr_ = tc::smem_u32(rpc);
+      constexpr int pa[6] = {0, 0, 1, 1, 0, 2}, pr[6] = {0, 1, 0, 1, 2, 0};
 #pragma unroll
-  for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {
-    const int e = tid + 256 * q, c = e / 32, r = 4 * (e % 32);
-    const bool in = i0 + r < n && j0 + c < n;
-    cp_async16(&si[c][r], in ? A + (i0 + r) + n * (j0 + c) : A, in);
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int ks = 0; ks < GJB / 16; ++ks)
+          tc::mma_bf16(tb, tc::sdesc(sa_ + pa[c] * kUtPiece + ks * 256, 128, 1024),
+                       tc::sdesc(sr_ + pr[c] * kUtPiece + ks * 256, 128, 1024), id,
+                       (kb | c | ks) ? 1u : 0u);
+      tc::mma_commit(&bar);
+    }
+    __syncwarp();
+    if (kb + 1 < nkb) {
+      ut_copy_slices(A, Rs, n, i0, j0, ko + int64_t(kb + 1) * GJB, sa, sr);
+    } else {                                       // the tile of A to subtract from, while the MMAs run
+#pragma unroll
+      for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {
+        const int e = tid + 256 * q, c = e / 32, r = 4 * (e % 32);
+        const bool in = i0 + r < n && j0 + c < n;
+        cp_async16(&si[c][r], in ? A + (i0 + r) + n * (j0 + c) : A, in);
+      }
+      cp_async_commit();
+    }
   }
-  cp_async_commit();
   cp_async_wait<0>();
-  const bool ok = __syncthreads_and(tc::mbar_wait(&bar, 0) ? 1 : 0) != 0;
+  const uint32_t tb = tbase_s;
+  if (ok) ok = __syncthreads_and(tc::mbar_wait(&bar, uint32_t(nkb - 1) & 1u) ? 1 : 0) != 0;
   if (ok) {
     tc::tc_fence_after();
     // warp w: TMEM lanes (rows) 32 (w % 4) .., columns 64 (w / 4) .. + 63;
@@ -600,7 +630,7 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* __restrict__ A, T
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int64_t j = j0 + c0 + c;
-        si[c0 + c][r] = ((j / GJB == k) ? 0.f : si[c0 + c][r]) - d[c];
+        si[c0 + c][r] = ((k >= 0 && j / GJB == k) ? 0.f : si[c0 + c][r]) - d[c];
       }
     }
   }
@@ -612,7 +642,7 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* __restrict__ A, T
       const int e = tid + 256 * q, c = e / 32, rr = 4 * (e % 32);
       const int64_t i = i0 + rr, j = j0 + c;
       const int64_t bi = i / GJB, bj = j / GJB;
-      if (i < n && j < n && bi != k && !(skip_pivot && bi == k + 1 && bj == k + 1))
+      if (i < n && j < n && !(k >= 0 && (bi == k || (skip_pivot && bi == k + 1 && bj == k + 1))))
         *reinterpret_cast<float4*>(B + i + n * j) = *reinterpret_cast<const float4*>(&si[c][rr]);
     }
   } else {
@@ -620,7 +650,8 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* __restrict__ A, T
       if (tmo) atomicAdd(tmo, 1);
       if (info) atomicCAS(info, 0, int(n + 1));
     }
-    tc::mbar_wait(&bar, 0);                        // the MMAs may still run: bounded drain
+    // the MMAs last committed may still run: bounded drain
+    tc::mbar_wait(&bar, uint32_t((kb < nkb ? kb : nkb) - 1) & 1u);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -638,13 +669,15 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* __restrict__ A, T
 // while it multiplies those of step kk.
 constexpr int kIdentSmem = 2 * 2 * GJB * GJP * 4;   // two stages of (Ls, Rc)
 template <typename T, bool ASYNC>
-__global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t n, int kb0, const int* skip) {
+__global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t n, int kb0, int border_only,
+                                                      const int* skip) {
   pdl_enter();
   if (skip && *skip) return;
   extern __shared__ __align__(16) float dsm[];
   const int nt = int((n + GJB - 1) / GJB);
   const int h = int(blockIdx.x) % 2, b = int(blockIdx.x) / 2;
   const int ti = b % nt, tj = b / nt;
+  if (border_only && ti >= kb0 && tj >= kb0) return;   // the trailing tiles: k_gj_update_tc
   const int bi = threadIdx.x % 8, bj = threadIdx.x / 8;
   const int64_t r0 = int64_t(ti) * GJB, c0 = int64_t(tj) * GJB + h * GJH;
   if (c0 >= n) return;
@@ -950,11 +983,19 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
       if (cudaFuncSetAttribute(k_gj_identity<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kIdentSmem) != cudaSuccess)
         return CP_ECUDA;
-      if (launch_pdl(k_gj_identity<T, true>, nt * nt * 2, GJTH, kIdentSmem, s, src, dst, n, k0, skip) != cudaSuccess)
+      if (launch_pdl(k_gj_identity<T, true>, nt * nt * 2, GJTH, kIdentSmem, s, src, dst, n, k0, use_tc ? 1 : 0,
+                     skip) != cudaSuccess)
         return CP_ECUDA;
+      if (use_tc) {
+        const int64_t base = int64_t(k0) * GJB;
+        const unsigned t = unsigned((n - base + kUtM - 1) / kUtM);
+        if (launch_pdl(k_gj_update_tc<T>, dim3(t, t), 256, kUtSmemAll, s, static_cast<const T*>(src), dst,
+                       static_cast<const T*>(src), n, base, int64_t(0), k0, -1, 0, skip, info, tmo) != cudaSuccess)
+          return CP_ECUDA;
+      }
     } else {
       if (launch_pdl(k_gj_identity<T, false>, nt * nt * 2, GJTH, (GJB * GJP + GJB * (GJH + 4)) * 4, s, src, dst, n,
-                     k0, skip) != cudaSuccess)
+                     k0, 0, skip) != cudaSuccess)
         return CP_ECUDA;
     }
     T* t = src;
@@ -983,8 +1024,9 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
                        : launch_pdl(k_gj_rowpanel<T, false>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk,
                                     skip) != cudaSuccess)
           return CP_ECUDA;
-        if (launch_pdl(k_gj_update_tc<T>, dim3(mt, ntc), 256, kUtSmemAll, s, src, dst, n, k, (next && side) ? 1 : 0,
-                       skip, info, tmo) != cudaSuccess)
+        if (launch_pdl(k_gj_update_tc<T>, dim3(mt, ntc), 256, kUtSmemAll, s, static_cast<const T*>(src), dst,
+                       static_cast<const T*>(dst), n, int64_t(0), int64_t(k) * GJB, 1, k, (next && side) ? 1 : 0, skip,
+                       info, tmo) != cudaSuccess)
           return CP_ECUDA;
       } else if (n % 4 == 0) {
         if (launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk, skip) !=
