@@ -979,7 +979,7 @@ def bench_batched(seed):
     b = cp.Batch([(p.Y, p.init, None) for p in probs], tol=1e-8, max_iter=1000)
     cfg = autotune.tune_batch(b, trials=2, cache=False)
     order = None if cfg["order"] == "given" else "cost"
-    g = b.capture(tile=cfg["tile"], order=order)
+    g = b.capture(tile=cfg["tile"], order=order, ctas=cfg["ctas"])
     times = []
     for rep in range(3):
         b.reset()
@@ -1018,7 +1018,7 @@ def bench_batched(seed):
     return {"oracle_final_eps_rel_err": {"max": max(errs), "sample": [int(k) for k in sample[:4]]},
             "workload": "512 problems, I_n~U{10..64}, R~U{3..12}, mode-1 collinearity 0.8, snr30, f32",
             "value": iters / t, "unit": "iters/s", "seconds_all_512": t, "problems_per_s": 512 / t,
-            "trials_total": iters, "stops": stops, "tile": cfg["tile"], "order": cfg["order"],
+            "trials_total": iters, "stops": stops, "tile": cfg["tile"], "order": cfg["order"], "ctas": cfg["ctas"], "tuner_timings_ms": cfg["timings"],
             "graph": "one captured persistent launch",
             "fp64_form": {"iters_per_s": it64 / t64, "seconds_per_problem": per64,
                           "sample": f"{len(sample)} problems run one at a time (float64 tensor, float64 core)"},

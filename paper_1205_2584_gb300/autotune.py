@@ -1,12 +1,15 @@
 """Autotuner for the batched form.
 
-The persistent batched launch has two knobs that change its speed but not its
-algebra: the number of fibres per tile of the in-CTA pass over each tensor
-(8, 16 or 32) and the order of the device work queue (as given, or most
-expensive problem first).  `tune_batch` times every candidate on the batch
-itself (a few trials per problem, from the batch's starting point, CUDA
-events), restores the starting point, and caches the fastest choice under a
-signature of the problem shapes.
+The persistent batched launch has three knobs that change its speed but not
+its algebra: the number of fibres per tile of the in-CTA pass over each
+tensor (8, 16 or 32), the order of the device work queue (as given, or most
+expensive problem first) and the number of persistent CTAs pulling from the
+queue (one or two per SM: a second CTA per SM hides the latency of the other's
+serial sections where shared memory lets both stay resident, and otherwise
+waits for the first).  `tune_batch` times every candidate on the batch itself
+(a few trials per problem, from the batch's starting point, CUDA events),
+restores the starting point, and caches the fastest choice under a signature
+of the problem shapes.
 """
 from __future__ import annotations
 
@@ -18,6 +21,7 @@ import torch
 
 TILES = (8, 16, 32)
 ORDERS = ("given", "cost")
+CTAS_PER_SM = (1, 2)
 _CACHE: Dict[str, dict] = {}
 
 
@@ -30,29 +34,32 @@ def signature(batch) -> str:
 
 
 def tune_batch(batch, trials: int = 2, repeats: int = 1, stream=None, cache: bool = True) -> dict:
-    """Return {"tile": t, "order": o, "ms": best, "timings": {...}} for `batch`."""
+    """Return {"tile": t, "order": o, "ctas": c, "ms": best, "timings": {...}} for `batch`."""
     key = signature(batch)
     if cache and key in _CACHE:
         return _CACHE[key]
     s = stream if stream is not None else torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     timings = {}
     for tile in TILES:
         for order in ORDERS:
-            best = None
-            for _ in range(repeats):
-                batch.reset()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(s)
-                batch.run(trials=trials, tile=tile, order=None if order == "given" else "cost", stream=s)
-                e1.record(s)
-                s.synchronize()
-                ms = e0.elapsed_time(e1)
-                best = ms if best is None else min(best, ms)
-            timings[f"{tile}/{order}"] = best
+            for per_sm in CTAS_PER_SM:
+                best = None
+                for _ in range(repeats):
+                    batch.reset()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    batch.run(trials=trials, ctas=per_sm * sms, tile=tile,
+                              order=None if order == "given" else "cost", stream=s)
+                    e1.record(s)
+                    s.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    best = ms if best is None else min(best, ms)
+                timings[f"{tile}/{order}/{per_sm * sms}"] = best
     batch.reset()
     k = min(timings, key=timings.get)
-    tile, order = k.split("/")
-    out = {"tile": int(tile), "order": order, "ms": timings[k], "timings": timings}
+    tile, order, ctas = k.split("/")
+    out = {"tile": int(tile), "order": order, "ctas": int(ctas), "ms": timings[k], "timings": timings}
     if cache:
         _CACHE[key] = out
     return out

@@ -420,15 +420,15 @@ class Batch:
                                  _ptr(self.status), ctypes.byref(self.opts), int(trials), int(ctas), int(tile),
                                  _ptr(order), _stream(stream)), "cp_batch_run")
 
-    def capture(self, trials: int = 1 << 30, tile: int = 0, order=None):
+    def capture(self, trials: int = 1 << 30, tile: int = 0, order=None, ctas: int = 0):
         """Capture one persistent launch (queue reset + kernel) in a CUDA graph;
         returns the torch.cuda.CUDAGraph (replay() runs it on the current stream)."""
-        self.run(trials=1, tile=tile, order=order)      # sets the kernel's shared-memory attribute
+        self.run(trials=1, tile=tile, order=order, ctas=ctas)   # sets the kernel's shared-memory attribute
         torch.cuda.synchronize()
         self.reset()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.run(trials=trials, tile=tile, order=order)
+            self.run(trials=trials, tile=tile, order=order, ctas=ctas)
         return g
 
     def cost_order(self):
@@ -454,7 +454,7 @@ class Batch:
         from . import autotune
         cfg = autotune.tune_batch(self, trials=tune_trials, stream=stream)
         self.run(trials=trials, tile=cfg["tile"], order=None if cfg["order"] == "given" else "cost",
-                 stream=stream)
+                 ctas=cfg["ctas"], stream=stream)
         return cfg
 
     def statuses(self):

@@ -45,6 +45,7 @@ import numpy as np
 
 _ALIGN = 256
 _PARKED = 3     # stop code kept by free descriptor slots (the kernel skips them)
+MAX_LARGE = 16  # large requests at once when their number is bounded by the budget alone
 
 
 # ---------------------------------------------------------------------------
@@ -433,7 +434,9 @@ class Server:
     lanes: (max_cost, slots, trials per round) per lane, cost = R prod(I_n);
     a request joins the first lane whose class holds it and whose shape the
     batched kernel takes, else it is a large request; at most large_slots
-    large requests run at once (they share the GPU).  All requests share the
+    large requests run at once (they share the GPU), or, with large_slots = 0,
+    as many as the large-request budget holds (at most MAX_LARGE).  All
+    requests share the
     stop rule (tol, mu_max, max_iter) and the kernel tile size, so a lane
     request's arithmetic is the same whatever else is in flight.
     """
@@ -507,7 +510,8 @@ class Server:
             # large requests: re-arm an idle slot of the same shape, or make a
             # slot within the budget (dropping idle slots of other shapes)
             q = waiting.get(-1, [])
-            while q and len(self.busy) < self.large_slots:
+            cap = self.large_slots if self.large_slots > 0 else MAX_LARGE
+            while q and len(self.busy) < cap:
                 slot = self._state_slot(q[0])
                 if slot is None:
                     break

@@ -131,11 +131,12 @@ def test_autotuner_choice_runs_and_matches(cp):
     probs = _problems(700, MIX)
     b = cp.Batch([(p.Y, p.init, 1.0) for p in probs], max_iter=40)
     cfg = autotune.tune_batch(b, trials=2, cache=False)
-    assert cfg["tile"] in (8, 16, 32) and cfg["order"] in ("given", "cost")
-    assert len(cfg["timings"]) == 6
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert cfg["tile"] in (8, 16, 32) and cfg["order"] in ("given", "cost") and cfg["ctas"] in (sms, 2 * sms)
+    assert len(cfg["timings"]) == 12
     st0 = b.statuses()
     assert all(s["iters"] == 0 for s in st0)
-    b.run(tile=cfg["tile"], order=None if cfg["order"] == "given" else "cost")
+    b.run(tile=cfg["tile"], order=None if cfg["order"] == "given" else "cost", ctas=cfg["ctas"])
     ref = cp.Batch([(p.Y, p.init, 1.0) for p in probs], max_iter=40)
     ref.run()
     torch.cuda.synchronize()

@@ -128,3 +128,23 @@ def test_realtime_arrivals_overlap(sv):
     assert s["p99_s"] >= s["p50_s"] > 0
     ad = sorted(r.admitted for r in res)
     assert ad[-1] - ad[0] > 0.02        # admitted over time, not all at once
+
+
+def test_budget_bound_large_slots(sv):
+    """large_slots = 0: as many large requests run at once as the large-request
+    budget holds (here three States of one shape); the others wait and every
+    request still finishes with the result it has alone."""
+    serve = sv
+    big = [_req(serve, k, 1200 + k, (300, 24, 20), 4)[0] for k in range(6)]
+    per_big = serve.state_bytes((300, 24, 20), 4)
+    arena = 1 << 20
+    srv = _server(serve, arena_bytes=arena, hbm_budget=arena + 3 * per_big + 1024, large_slots=0)
+    res = {r.rid: r for r in srv.serve(big, realtime=False)}
+    assert sorted(res) == list(range(6))
+    assert srv.peak_busy == 3
+    assert srv.peak_bytes <= srv.budget
+    srv.close()
+    srv = _server(serve)
+    alone = srv.serve([big[4]], realtime=False)[0]
+    srv.close()
+    assert alone.status["rel_err"] == pytest.approx(res[4].status["rel_err"], rel=1e-6)
