@@ -228,6 +228,7 @@ __device__ void factor_store(double* A, int64_t n, int kk, double* dinv, int* in
 // by every CTA from the stored L_kk.
 __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* dinv, int* info, CholSync* sy,
                                                int* tmo, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ double D[CB][CB + 1];
   __shared__ double rinv[CB];
@@ -352,6 +353,7 @@ __global__ void __launch_bounds__(CT) k_chol64(double* A, int64_t n, double* din
 __global__ void __launch_bounds__(CT) k_trsv64(const double* L, const double* dinv, int64_t n, const double* b,
                                                double* x, int backward, CholSync* sy, int* info, int* tmo,
                                                const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ int s_c;
   __shared__ double part[8][CB];
@@ -490,7 +492,7 @@ int chol64_factor(double* A, int64_t n, double* dinv, int* info, void* sync, int
   if (rows > want) want = rows;
   if (want < 1) want = 1;
   if (G > want) G = int(want);
-  k_chol64<<<G, CT, 0, s>>>(A, n, dinv, info, sy, tmo, skip);
+  CP_CUDA(launch_pdl(k_chol64, G, CT, 0, s, A, n, dinv, info, sy, tmo, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -500,9 +502,9 @@ int chol64_solve(const double* L, const double* dinv, int64_t n, const double* b
   CholSync* sy = static_cast<CholSync*>(sync);
   const int nb = int((n + CB - 1) / CB);
   if (cudaMemsetAsync(sy, 0, chol64_sync_bytes(n), s) != cudaSuccess) return CP_ECUDA;
-  k_trsv64<<<nb, CT, 0, s>>>(L, dinv, n, b, z, 0, sy, info, tmo, skip);
+  CP_CUDA(launch_pdl(k_trsv64, nb, CT, 0, s, L, dinv, n, b, z, 0, sy, info, tmo, skip));
   if (cudaMemsetAsync(sy, 0, chol64_sync_bytes(n), s) != cudaSuccess) return CP_ECUDA;
-  k_trsv64<<<nb, CT, 0, s>>>(L, dinv, n, z, y, 1, sy, info, tmo, skip);
+  CP_CUDA(launch_pdl(k_trsv64, nb, CT, 0, s, L, dinv, n, z, y, 1, sy, info, tmo, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 

@@ -186,6 +186,37 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// Programmatic dependent launch.  The step's kernels are launched with the
+// programmatic-serialisation attribute (launch_pdl), so a kernel's CTAs may be
+// scheduled while its predecessor on the stream still runs.  Every such
+// kernel begins with pdl_enter(): each CTA first waits (griddepcontrol.wait)
+// until the predecessor has completed and its writes are visible, before it
+// reads anything (the skip flag included) or exits, so each kernel completes
+// after its predecessor and the ordering stays transitive; it then lets its
+// own successor be scheduled.  A successor is scheduled only once every CTA
+// of the kernel has started, so a grid whose CTAs wait on one another (all
+// resident at once) is never crowded out by it.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 }  // namespace cpdgn
 
 #define CP_TRY(expr)                   \

@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
                                                             const double* mu, double* Gnm, double* Gt,
                                                             double* U, double* LC, double* w, int* info,
                                                             const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ double G[kRR], Gam[kRR], Cn[kRR], Pn[kRR];
   __shared__ double z[CP_MAX_R], u[CP_MAX_R], v[CP_MAX_R], rinv[CP_MAX_R];
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
 int launch_mode_prep(const Dims& d, const double* C, const double* P, const double* mu, double* Gnm,
                      double* Gt, double* U, double* LC, double* w, int* info, const int* skip,
                      cudaStream_t s) {
-  k_mode_prep<<<d.N * d.R + d.N, kPrepThreads, 0, s>>>(d, C, P, mu, Gnm, Gt, U, LC, w, info, skip);
+  CP_CUDA(launch_pdl(k_mode_prep, d.N * d.R + d.N, kPrepThreads, 0, s, d, C, P, mu, Gnm, Gt, U, LC, w, info, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -147,6 +148,7 @@ __device__ __forceinline__ void pair_of(int p, int* n, int* m) {
 // CTA (pair p, j): W_nm[a + R (k + R j)] = sum_b Gamma^(n,m)[a,b] L_m[b,k] U_n[b,j].
 __global__ void __launch_bounds__(256) k_core_w(Dims d, const double* Gnm, const double* LC,
                                                 const double* U, double* Wp, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ double G[kRR], Lm[kRR], un[CP_MAX_R];
   const int R = d.R, RR = d.RR, N = d.N;
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(256) k_core_w(Dims d, const double* Gnm, const
 template <typename T>
 __global__ void k_core_fill(Dims d, const double* LC, const double* U, const double* Wp, T* core,
                             int64_t ld, int full, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int R = d.R, RR = d.RR, N = d.N;
   const int npairs = N * (N - 1) / 2;
@@ -214,7 +217,7 @@ int launch_core_w(const Dims& d, const double* Gnm, const double* LC, const doub
                   const int* skip, cudaStream_t s) {
   const int npairs = d.N * (d.N - 1) / 2;
   if (npairs == 0) return CP_OK;
-  k_core_w<<<npairs * d.R, 256, 0, s>>>(d, Gnm, LC, U, Wp, skip);
+  CP_CUDA(launch_pdl(k_core_w, npairs * d.R, 256, 0, s, d, Gnm, LC, U, Wp, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -223,7 +226,7 @@ int launch_core_fill(const Dims& d, const double* LC, const double* U, const dou
                      const int* skip, cudaStream_t s) {
   const int npairs = d.N * (d.N - 1) / 2;
   int threads = ((d.RR + 31) / 32) * 32;
-  k_core_fill<T><<<(npairs + d.N) * d.RR, threads, 0, s>>>(d, LC, U, Wp, core, d.ncore, full, skip);
+  CP_CUDA(launch_pdl(k_core_fill<T>, (npairs + d.N) * d.RR, threads, 0, s, d, LC, U, Wp, core, d.ncore, full, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 template int launch_core_fill<double>(const Dims&, const double*, const double*, const double*, double*,
@@ -252,6 +255,7 @@ __device__ void stage_Kx(const Dims& d, int n, int jmax, const double* Gnm, cons
 // out = K x (base == null) or out = base - K x; one thread per entry.
 __global__ void k_apply_K(Dims d, const double* Gnm, const double* x, const double* base, double* out,
                           const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int R = d.R, RR = d.RR, N = d.N;
   int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -275,6 +279,7 @@ static_assert(kOpWarps == 4, "the partial sums below are added as four terms");
 // out_m = vec(L_m X_m U_m^T): CTA (m, q) computes column q.
 __global__ void __launch_bounds__(kOpThreads) k_apply_S(Dims d, const double* LC, const double* U,
                                                         const double* x, double* out, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ double X[kRR], L[kRR], uq[CP_MAX_R], t[CP_MAX_R];
   __shared__ double part[2][kOpWarps][CP_MAX_R];
@@ -313,6 +318,7 @@ __global__ void __launch_bounds__(kOpThreads) k_apply_ST(Dims d, const double* L
                                                          const double* Gnm, const double* x, int kx,
                                                          const double* b, const double* y, double* out,
                                                          double* kw, double* norm2, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ double V[kRR], L[kRR], uq[CP_MAX_R], t[CP_MAX_R];
   __shared__ double part[2][kOpWarps][CP_MAX_R];
@@ -361,18 +367,18 @@ __global__ void __launch_bounds__(kOpThreads) k_apply_ST(Dims d, const double* L
 
 int launch_apply_K(const Dims& d, const double* Gnm, const double* x, const double* base, double* out,
                    const int* skip, cudaStream_t s) {
-  k_apply_K<<<unsigned((d.ncore + 127) / 128), 128, 0, s>>>(d, Gnm, x, base, out, skip);
+  CP_CUDA(launch_pdl(k_apply_K, unsigned((d.ncore + 127) / 128), 128, 0, s, d, Gnm, x, base, out, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 int launch_apply_S(const Dims& d, const double* LC, const double* U, const double* x, double* out,
                    const int* skip, cudaStream_t s) {
-  k_apply_S<<<d.N * d.R, kOpThreads, 0, s>>>(d, LC, U, x, out, skip);
+  CP_CUDA(launch_pdl(k_apply_S, d.N * d.R, kOpThreads, 0, s, d, LC, U, x, out, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 int launch_apply_ST(const Dims& d, const double* LC, const double* U, const double* Gnm, const double* x,
                     int kx, const double* b, const double* y, double* out, double* kw, double* norm2,
                     const int* skip, cudaStream_t s) {
-  k_apply_ST<<<d.N * d.R, kOpThreads, 0, s>>>(d, LC, U, Gnm, x, kx, b, y, out, kw, norm2, skip);
+  CP_CUDA(launch_pdl(k_apply_ST, d.N * d.R, kOpThreads, 0, s, d, LC, U, Gnm, x, kx, b, y, out, kw, norm2, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 

@@ -53,17 +53,6 @@ constexpr int kPivotReserve = 168 * 1024;
 // refinement, so the fast intrinsic division (about 2 ulp) is accurate enough.
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 
-// Programmatic dependent launch.  The sweep kernels are launched with the
-// programmatic-serialisation attribute, so a kernel's CTAs may be scheduled
-// while its predecessor on the stream still runs.  Every CTA first waits
-// (griddepcontrol.wait) until the predecessor has completed and its writes
-// are visible, before it reads anything (the skip flag included) or exits,
-// so each kernel completes after its predecessor and the ordering is
-// transitive.  It then lets its own successor be scheduled.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
 
 // S[c][r] = sgn * A(r0 + r, c0 + c) for r, c < 64 (zero outside n x n): a
 // 64 x 64 left operand stored column by column.  Global reads are coalesced
@@ -931,23 +920,6 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, c
   pivot_store(x, n, k1, kb, Pinv_next, A, info, prow, pcol, &bad);
 }
 
-// Launch with the programmatic-serialisation attribute (see pdl_enter).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s,
-                              Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
-
 // Invert the n x n SPD matrix A (full storage, column-major); B is the second
 // buffer and pinv holds 2 GJB x GJB blocks.  *result receives the buffer with
 // the inverse.  When the leading `ident` rows/columns of A are the identity,
@@ -1070,6 +1042,7 @@ constexpr int GVS = 64;     // columns per slice
 __global__ void __launch_bounds__(GVT) k_gemv_acc(const float* X, int64_t n, const double* r, double* y,
                                                   const double* b2, const double* r2, const double* r2prev,
                                                   int* done, double tol2, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   if (b2 && r2) {
     const double vb = *b2, vr = *r2, vp = r2prev ? *r2prev : 0.0;
@@ -1102,7 +1075,7 @@ __global__ void __launch_bounds__(GVT) k_gemv_acc(const float* X, int64_t n, con
 int launch_gemv_acc(const float* X, int64_t n, const double* r, double* y, const double* b2, const double* r2,
                     const double* r2prev, int* done, double tol2, const int* skip, cudaStream_t s) {
   dim3 g(unsigned((n + GVT - 1) / GVT), unsigned((n + GVS - 1) / GVS));
-  k_gemv_acc<<<g, GVT, 0, s>>>(X, n, r, y, b2, r2, r2prev, done, tol2, skip);
+  CP_CUDA(launch_pdl(k_gemv_acc, g, GVT, 0, s, X, n, r, y, b2, r2, r2prev, done, tol2, skip));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 

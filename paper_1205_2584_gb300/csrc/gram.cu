@@ -25,6 +25,7 @@ __host__ __device__ inline int gram_entries(int R, bool withP) { return R * (R +
 
 __global__ void __launch_bounds__(kGramThreads) k_gram_partial(Dims d, const double* a, const double* m,
                                                                double* part, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ double As[kGramRows][CP_MAX_R + 1];
   __shared__ double Ms[kGramRows][CP_MAX_R + 1];
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_partial(Dims d, const dou
 // C^(n) (mirrored) and P^(n) from the partials, summed in chunk order.
 __global__ void k_gram_reduce(Dims d, const double* part, bool withP, double* C, double* P,
                               const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int R = d.R, RR = d.RR;
   const int nC = R * (R + 1) / 2;
@@ -101,6 +103,7 @@ __global__ void k_gram_reduce(Dims d, const double* part, bool withP, double* C,
 
 // Gamma^(n,m) for all n, m and Gamma (one thread per entry).
 __global__ void k_gram_hadamard(Dims d, const double* C, double* Gnm, double* Gall, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int RR = d.RR, N = d.N;
   int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -129,12 +132,12 @@ size_t gram_part_bytes(const Dims& d) {
 int launch_gram(const Dims& d, const double* a, const double* m, double* part, double* C, double* P,
                 double* Gnm, double* Gall, const int* skip, cudaStream_t s) {
   const int64_t nch = gram_chunks(d);
-  k_gram_partial<<<unsigned(nch), kGramThreads, 0, s>>>(d, a, m, part, skip);
+  CP_CUDA(launch_pdl(k_gram_partial, unsigned(nch), kGramThreads, 0, s, d, a, m, part, skip));
   const int64_t ne = int64_t(d.N) * gram_entries(d.R, m != nullptr);
-  k_gram_reduce<<<unsigned((ne + 127) / 128), 128, 0, s>>>(d, part, m != nullptr, C, P, skip);
+  CP_CUDA(launch_pdl(k_gram_reduce, unsigned((ne + 127) / 128), 128, 0, s, d, part, m != nullptr, C, P, skip));
   if (Gnm || Gall) {
     const int64_t nH = int64_t(d.N) * d.N * d.RR + d.RR;
-    k_gram_hadamard<<<unsigned((nH + 127) / 128), 128, 0, s>>>(d, C, Gnm, Gall, skip);
+    CP_CUDA(launch_pdl(k_gram_hadamard, unsigned((nH + 127) / 128), 128, 0, s, d, C, Gnm, Gall, skip));
   }
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }

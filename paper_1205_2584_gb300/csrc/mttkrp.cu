@@ -45,6 +45,7 @@ constexpr int kMtThreads = 256;
 
 template <typename TY, typename TA, int RMAX>
 __global__ void __launch_bounds__(kMtThreads) k_mttkrp(MttkrpParams p) {
+  pdl_enter();
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims& d = p.d;
@@ -303,6 +304,7 @@ __device__ void tile_copy(const TY* Y, int64_t f0, int nf, int I1, int ldy, TT* 
 
 template <typename TY, typename TT, typename TA, int RMAX, int RPT>
 __global__ void __launch_bounds__(kT2) k_mttkrp_tiled(Tiled p) {
+  pdl_enter();
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims& d = p.d;
@@ -597,6 +599,7 @@ __device__ __forceinline__ void tile_copy3<__nv_bfloat16>(const __nv_bfloat16* Y
 
 template <typename TY, int PB>
 __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
+  pdl_enter();
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims& d = p.d;
@@ -875,7 +878,7 @@ static int launch3_t(const P3& p, int grid, size_t smem, cudaStream_t s) {
   auto kern = k_mttkrp3<TY, PB>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
     return CP_ECUDA;
-  kern<<<grid, kT3, smem, s>>>(p);
+  CP_CUDA(launch_pdl(kern, grid, kT3, smem, s, p));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -974,7 +977,7 @@ static int launch_t(const MttkrpParams& p, int grid, size_t smem, cudaStream_t s
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
       return CP_ECUDA;
   }
-  kern<<<grid, kMtThreads, smem, s>>>(p);
+  CP_CUDA(launch_pdl(kern, grid, kMtThreads, smem, s, p));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -1003,7 +1006,7 @@ static int launch_tiled_t(const Tiled& p, int grid, size_t smem, cudaStream_t s)
   auto kern = k_mttkrp_tiled<TY, TT, TA, RMAX, RPT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
     return CP_ECUDA;
-  kern<<<grid, kT2, smem, s>>>(p);
+  CP_CUDA(launch_pdl(kern, grid, kT2, smem, s, p));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -1159,6 +1162,7 @@ extern "C" int cp_mttkrp_all(const cp_shape* shape, const void* Y, const double*
 
 namespace cpdgn {
 __global__ void k_rel_err(const double* resid2, double y_norm2, double* rel) {
+  pdl_enter();
   if (threadIdx.x == 0 && blockIdx.x == 0) *rel = sqrt(*resid2 / y_norm2);
 }
 }  // namespace cpdgn
@@ -1174,7 +1178,7 @@ extern "C" int cp_fit(const cp_shape* shape, const void* Y, const double* a, dou
   CP_CUDA(cudaMemsetAsync(resid2, 0, sizeof(double), s));
   CP_TRY(launch_mttkrp(d, Y, a, nullptr, resid2, nullptr, s, 0));
   if (rel_err && y_norm2 > 0) {
-    k_rel_err<<<1, 32, 0, s>>>(resid2, y_norm2, rel_err);
+    CP_CUDA(launch_pdl(k_rel_err, 1, 32, 0, s, resid2, y_norm2, rel_err));
     if (cudaGetLastError() != cudaSuccess) return CP_ECUDA;
   }
   return CP_OK;

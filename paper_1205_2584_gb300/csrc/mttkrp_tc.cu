@@ -178,6 +178,7 @@ __device__ __forceinline__ void build_w(unsigned char* wbuf, const float (&a2)[3
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_constant__ CUtensorMap tmap, TcParams p) {
+  pdl_enter();
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t bar_full[kSlots], bar_empty[kSlots];
@@ -546,6 +547,7 @@ __device__ __forceinline__ bool epi_all(bool v) {
 __global__ void __launch_bounds__(kTcThreads3, 1)
     k_mttkrp_tc3(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CUtensorMap tmap_lo,
                  Tc3Params p3) {
+  pdl_enter();
   const TcParams& p = p3.t;
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -888,7 +890,7 @@ bool tc_disabled() {
 int launch_tc(const CUtensorMap& tm, const TcParams& p, int grid, cudaStream_t s) {
   if (cudaFuncSetAttribute(k_mttkrp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTc) != cudaSuccess)
     return CP_ECUDA;
-  k_mttkrp_tc<<<grid, kTcThreads, kSmemTc, s>>>(tm, p);
+  CP_CUDA(launch_pdl(k_mttkrp_tc, grid, kTcThreads, kSmemTc, s, tm, p));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -935,7 +937,7 @@ static int launch_tc3(const Dims& d, const void* Y, const double* a, double* m, 
   if (grid > (int64_t(1) << 31) - 1) return CP_EINVAL;
   if (cudaFuncSetAttribute(k_mttkrp_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTc3) != cudaSuccess)
     return CP_ECUDA;
-  k_mttkrp_tc3<<<int(grid), kTcThreads3, kSmemTc3, s>>>(tm[0], tm[1], p3);
+  CP_CUDA(launch_pdl(k_mttkrp_tc3, int(grid), kTcThreads3, kSmemTc3, s, tm[0], tm[1], p3));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 

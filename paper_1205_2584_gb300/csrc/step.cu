@@ -124,6 +124,7 @@ static Bufs carve(const Layout& L, void* ws, int64_t ncore) {
 // ---------------------------------------------------------------------------
 
 __global__ void k_step_begin(int64_t nm, double* mt, double* scal, int* info, const cp_status* st) {
+  pdl_enter();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i == 0) {
     info[IN_INFO] = 0;
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(kUpdRows * 32) k_update(Dims d, const double* 
                                                           const double* f, const double* mu,
                                                           double* delta, double* at, double* part,
                                                           const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ double Gam[CP_MAX_R * CP_MAX_R], Fn[CP_MAX_R * CP_MAX_R], Gtn[CP_MAX_R * CP_MAX_R];
   __shared__ double Arow[kUpdRows][CP_MAX_R], H[kUpdRows][CP_MAX_R], Q[kUpdRows][CP_MAX_R];
@@ -206,6 +208,7 @@ __global__ void __launch_bounds__(kUpdRows * 32) k_update(Dims d, const double* 
 
 __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_status* st,
                           double* scal, int* info, double* scale, const int* tmo) {
+  pdl_enter();
   // One CTA of 256 threads.  The float64 square roots, divides and roots
   // below are long dependent operations on this part (hundreds of cycles
   // each), so independent ones run on different threads: the two relative
@@ -334,6 +337,7 @@ __global__ void k_control(Dims d, cp_opts o, double* part, int64_t nparts, cp_st
 
 __global__ void k_commit(Dims d, const int* commit, const double* at, const double* mt,
                          const double* scale, double* a, double* m) {
+  pdl_enter();
   if (!*commit) return;
   const int64_t tot = d.T * d.R;
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < tot;
@@ -348,6 +352,7 @@ __global__ void k_commit(Dims d, const int* commit, const double* at, const doub
 }
 
 __global__ void k_sumsq(const void* Y, int dtype, int64_t J, double* out) {
+  pdl_enter();
   __shared__ double sh[256];
   double s = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < J; i += int64_t(gridDim.x) * 256) {
@@ -366,6 +371,7 @@ __global__ void k_sumsq(const void* Y, int dtype, int64_t J, double* out) {
 
 __global__ void k_init_status(Dims d, cp_opts o, const double* Gnm, const double* scal, cp_status* st,
                               double* mu_copy, const int* tmo, int* info) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double mx = 0.0;
   for (int n = 0; n < d.N; ++n)
@@ -427,6 +433,7 @@ static int core_rhs(const Dims& d, const Bufs& B, const int* skip, cudaStream_t 
 // path below runs for this trial.
 __global__ void k_refine_verdict(const double* nrm, int K, double tol2, const int* stop, const int* info32,
                                  int* skip64) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int out = 1;
   if (*stop == CP_RUNNING) {
@@ -484,7 +491,7 @@ static int solve_core(const Dims& d, const Bufs& B, double* core64, const float*
       // bfloat16 tensors, whose gradient blocks carry float32-level rounding
       // already (a tighter core solve would not make the step more accurate)
       const double tol2 = (d.y_dtype == CP_F64) ? 1e-28 : 1e-16;
-      k_refine_verdict<<<1, 32, 0, s>>>(nrm, K, tol2, skip, B.info + IN_INFO32, B.info + IN_SKIP64);
+      CP_CUDA(launch_pdl(k_refine_verdict, 1, 32, 0, s, nrm, K, tol2, skip, B.info + IN_INFO32, B.info + IN_SKIP64));
       CP_TRY(solve_core_f64(d, B, core64, tmo, B.info + IN_SKIP64, s, true));
     }
   }
@@ -746,9 +753,9 @@ extern "C" int cp_state_init(cp_state* st, const void* Y, void* stream) {
   CP_TRY(launch_mttkrp(d, Y, st->a, B.m, B.scal + SC_R2, nullptr, s, d.mg));
   int64_t g = (d.J + 255) / 256;
   if (g > 4 * kSMs) g = 4 * kSMs;
-  k_sumsq<<<unsigned(g), 256, 0, s>>>(Y, d.y_dtype, d.J, B.scal + SC_YN2);
+  CP_CUDA(launch_pdl(k_sumsq, unsigned(g), 256, 0, s, Y, d.y_dtype, d.J, B.scal + SC_YN2));
   CP_TRY(launch_gram(d, st->a, nullptr, B.gpart, B.C, nullptr, B.Gnm, B.Gall, nullptr, s));
-  k_init_status<<<1, 32, 0, s>>>(d, st->o, B.Gnm, B.scal, B.status, B.mu, st->tmo, B.info);
+  CP_CUDA(launch_pdl(k_init_status, 1, 32, 0, s, d, st->o, B.Gnm, B.scal, B.status, B.mu, st->tmo, B.info));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
@@ -760,8 +767,8 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
   const int* skip = &B.status->stop;
   const double* mu = &B.status->mu;
   const int64_t nm = d.T * d.R;
-  k_step_begin<<<unsigned((nm + 255) / 256 < 64 ? (nm + 255) / 256 : 64), 256, 0, s>>>(nm, B.mt, B.scal,
-                                                                                       B.info, B.status);
+  CP_CUDA(launch_pdl(k_step_begin, unsigned((nm + 255) / 256 < 64 ? (nm + 255) / 256 : 64), 256, 0, s, nm, B.mt, B.scal,
+                                                                                       B.info, B.status));
   CP_TRY(launch_gram(d, st->a, B.m, B.gpart, B.C, B.P, nullptr, nullptr, skip, s));
   CP_TRY(launch_mode_prep(d, B.C, B.P, mu, B.Gnm, B.Gt, B.U, B.LC, B.w, B.info + IN_INFO, skip, s));
   CP_TRY(launch_core_w(d, B.Gnm, B.LC, B.U, B.Wp, skip, s));
@@ -787,13 +794,13 @@ extern "C" int cp_dgn_step(cp_state* st, const void* Y, void* stream) {
                       skip, s, true));
   }
   const int64_t nupd = update_ctas(d);
-  k_update<<<unsigned(nupd), kUpdRows * 32, 0, s>>>(d, st->a, B.m, B.Gnm, B.Gt, B.f, mu, B.delta, B.at,
-                                                    B.part, skip);
+  CP_CUDA(launch_pdl(k_update, unsigned(nupd), kUpdRows * 32, 0, s, d, st->a, B.m, B.Gnm, B.Gt, B.f, mu, B.delta, B.at,
+                                                    B.part, skip));
   CP_TRY(launch_mttkrp(d, Y, B.at, B.mt, B.scal + SC_R2T, skip, s, d.mg));
-  k_control<<<1, 256, 0, s>>>(d, st->o, B.part, nupd, B.status, B.scal, B.info, B.scale, st->tmo);
+  CP_CUDA(launch_pdl(k_control, 1, 256, 0, s, d, st->o, B.part, nupd, B.status, B.scal, B.info, B.scale, st->tmo));
   int64_t gc = (nm + 255) / 256;
   if (gc > 4 * kSMs) gc = 4 * kSMs;
-  k_commit<<<unsigned(gc), 256, 0, s>>>(d, B.info + IN_COMMIT, B.at, B.mt, B.scale, st->a, B.m);
+  CP_CUDA(launch_pdl(k_commit, unsigned(gc), 256, 0, s, d, B.info + IN_COMMIT, B.at, B.mt, B.scale, st->a, B.m));
   return cudaGetLastError() == cudaSuccess ? CP_OK : CP_ECUDA;
 }
 
