@@ -57,7 +57,7 @@ TRAFFIC_TC3_512 = 537.898752e6 + 2.792192e6   # k_mttkrp_tc3, 512^3 R=32
 TRAFFIC_TC_200 = None                  # k_mttkrp_tc, 200^3 R=20, float32 tensor
 # summed over the kernels of one float32 core inverse (n = 1200), every kernel
 # with cold caches under ncu (bytes)
-GJ_TRAFFIC = 88.605952e6
+GJ_TRAFFIC = 95.024128e6
 # timed runs restart from their initial factors every this many launches
 RESTART_EVERY = 50
 
