@@ -85,13 +85,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_mode_prep(Dims d, const double
   }
   const bool okG = cta_chol(G, rinv, R, &okc);
   if (tid == 0 && j == 0 && info && !okG) atomicCAS(info, 0, n + 1);
-  if (warp == 0) {
-    if (lane < R) z[lane] = (lane == j) ? 1.0 : 0.0;
-    warp_fwd(G, rinv, z, R);
-    warp_bwd(G, rinv, z, R);   // z = Gt e_j
-  } else if (warp == 1) {
-    if (lane < R) u[lane] = (lane == j) ? 1.0 : 0.0;
-    warp_bwd(G, rinv, u, R);   // u = L_G^{-T} e_j, concurrently with z
+  if (warp < 2) {                 // warp 0: z = Gt e_j; warp 1: u = L_G^{-T} e_j, concurrently
+    const double rl = lane < R ? rinv[lane] : 1.0;
+    double x = (lane == j) ? 1.0 : 0.0;
+    if (warp == 0) x = warp_fwd_reg(G, rl, x, R);
+    x = warp_bwd_reg(G, rl, x, R);
+    if (lane < R) (warp == 0 ? z : u)[lane] = x;
   }
   __syncthreads();
   // the three length-R dot products per entry below are float64 chains of

@@ -36,64 +36,96 @@ __device__ __forceinline__ bool warp_chol(double* G, double* rinv, int R) {
   return ok;
 }
 
-// The same factorisation by a whole CTA.  The pivot chain is latency-bound:
-// on this part a dependent float64 square root costs about 560 cycles and a
-// divide about 360, a reciprocal square root about 320.  So one thread takes
-// rsqrt of each pivot (L[k,k] = piv * rsqrt(piv), 1 / L[k,k] = rsqrt(piv),
-// each within a few ulp of the square root and its reciprocal) while the
-// others wait at a barrier, and the column scale and the trailing update are
-// spread over all threads.  ok_s is a shared-memory flag; the return value is
-// uniform over the CTA.
+// 1 / d for d > 0 (finite) by Newton's iteration for the reciprocal,
+// x <- x (2 - d x), written as x + x (1 - d x), from the hardware's
+// approximate double reciprocal: two iterations take its error below the
+// rounding of a double, in four dependent multiply-adds.
+__device__ __forceinline__ double small_recip(double d) {
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+  x = fma(x, fma(-d, x, 1.0), x);
+  x = fma(x, fma(-d, x, 1.0), x);
+  return x;
+}
+
+// The same factorisation by a whole CTA (R <= 32, at least R threads).  The
+// pivot chain is latency-bound: on this part a dependent float64 square root
+// costs about 560 cycles, a reciprocal square root about 320.  So the
+// elimination keeps each column unscaled, D[i][l] -= D[i][k] D[l][k] / d_k for
+// k < l <= i, which needs only the reciprocal of each pivot: the thread that
+// updates the next pivot forms it at once (small_recip), and one barrier per
+// column separates the steps.  Lane = row i, the warps share the columns l.
+// At the end L[i][k] = D[i][k] / sqrt(d_k) for all entries at once, with
+// rinv[k] = 1 / sqrt(d_k).  A non-positive or non-finite pivot clears *ok_s
+// and is replaced by 1, so no NaN spreads; the return value is uniform over
+// the CTA.
 __device__ __forceinline__ bool cta_chol(double* G, double* rinv, int R, int* ok_s) {
+  __shared__ double q[CP_MAX_R];
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) *ok_s = 1;
-  for (int k = 0; k < R; ++k) {
-    __syncthreads();
-    if (tid == 0) {
-      const double piv = G[k + R * k];
-      if (!(piv > 0.0) || !isfinite(piv)) *ok_s = 0;
-      const double ik = rsqrt(piv);
-      G[k + R * k] = piv * ik;
-      rinv[k] = ik;
+  const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+  __syncthreads();
+  if (tid == 0) {
+    *ok_s = 1;
+    double d = G[0];
+    if (!(d > 0.0) || !isfinite(d)) {
+      *ok_s = 0;
+      d = 1.0;
+      G[0] = 1.0;
+    }
+    q[0] = small_recip(d);
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < R; ++k) {
+    const int i = k + 1 + lane;
+    if (i < R) {
+      const double gik = G[i + R * k] * q[k];
+      for (int l = k + 1 + w; l <= i; l += nw) {
+        const double v = fma(-gik, G[l + R * k], G[i + R * l]);
+        if (l == k + 1 && i == k + 1) {              // the next pivot: its reciprocal now
+          double d = v;
+          if (!(d > 0.0) || !isfinite(d)) {
+            *ok_s = 0;
+            d = 1.0;
+          }
+          G[i + R * l] = d;
+          q[k + 1] = small_recip(d);
+        } else {
+          G[i + R * l] = v;
+        }
+      }
     }
     __syncthreads();
-    const double ik = rinv[k];
-    const int m = R - k - 1;
-    for (int i = tid; i < m; i += nt) G[k + 1 + i + R * k] *= ik;
-    __syncthreads();
-    for (int q = tid; q < m * m; q += nt) {
-      const int i = k + 1 + q % m, l = k + 1 + q / m;
-      if (l <= i) G[i + R * l] = fma(-G[i + R * k], G[l + R * k], G[i + R * l]);
-    }
+  }
+  if (tid < R) rinv[tid] = rsqrt(G[tid + R * tid]);
+  __syncthreads();
+  for (int e = tid; e < R * R; e += nt) {
+    const int i = e % R, k = e / R;
+    if (i >= k) G[e] *= rinv[k];                     // L[k][k] = d_k / sqrt(d_k)
   }
   __syncthreads();
   return *ok_s != 0;
 }
 
-// z <- L^{-1} z, one warp; rinv = 1 / diag(L).
-__device__ __forceinline__ void warp_fwd(const double* L, const double* rinv, double* z, int R) {
+// z <- L^{-1} z and z <- L^{-T} z by one warp with z in registers (lane = row,
+// R <= 32): each step broadcasts one entry by a shuffle, so the chain per row
+// is a shuffle, a multiply and a multiply-add.  rl = rinv[lane] (1 / L[lane,lane]).
+__device__ __forceinline__ double warp_fwd_reg(const double* L, double rl, double z, int R) {
   const int lane = threadIdx.x & 31;
   for (int p = 0; p < R; ++p) {
-    __syncwarp();
-    const double zp = z[p] * rinv[p];
-    __syncwarp();
-    if (lane == p) z[p] = zp;
-    if (lane > p && lane < R) z[lane] = fma(-L[lane + R * p], zp, z[lane]);
+    const double zp = __shfl_sync(0xffffffffu, z, p) * __shfl_sync(0xffffffffu, rl, p);
+    if (lane == p) z = zp;
+    else if (lane > p && lane < R) z = fma(-L[lane + R * p], zp, z);
   }
-  __syncwarp();
+  return z;
 }
-
-// z <- L^{-T} z, one warp.
-__device__ __forceinline__ void warp_bwd(const double* L, const double* rinv, double* z, int R) {
+__device__ __forceinline__ double warp_bwd_reg(const double* L, double rl, double z, int R) {
   const int lane = threadIdx.x & 31;
   for (int p = R - 1; p >= 0; --p) {
-    __syncwarp();
-    const double zp = z[p] * rinv[p];
-    __syncwarp();
-    if (lane == p) z[p] = zp;
-    if (lane < p) z[lane] = fma(-L[p + R * lane], zp, z[lane]);
+    const double zp = __shfl_sync(0xffffffffu, z, p) * __shfl_sync(0xffffffffu, rl, p);
+    if (lane == p) z = zp;
+    else if (lane < p) z = fma(-L[p + R * lane], zp, z);
   }
-  __syncwarp();
+  return z;
 }
 
 }  // namespace cpdgn
