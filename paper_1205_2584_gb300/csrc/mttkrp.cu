@@ -566,7 +566,18 @@ struct P3 {
   int TF, ldy, Rp, ldi, nrb, npairB, FS;
   int mn2_smem;           // 1: mode-2 partial in shared memory
   int grad;               // 1: accumulate e = y - y_hat instead of y
+  int fast;               // 1: factor rows of modes 2..N and the partials of M_2..M_N in shared memory
+  int fib32;              // 1: fibre numbers fit 32 bits
+  int afoff[CP_MAX_N];    // fast: offset (floats) of mode k's rows (I_k x Rp) in the factor area
+  int mhoff[CP_MAX_N];    // fast: offset (floats) of mode n's partial (I_n x R) in the partial area
+  int af_size, mh_size;   // fast: floats of the two areas
 };
+
+// bfloat16 tiles are fetched 16 bytes (8 values) at a time into registers at
+// the top of a tile and written to the other tile buffer as float32 at its
+// end, so the loads of tile t + 1 overlap the products of tile t.  A tile of
+// at most kPref3 * kT3 * 8 values takes this path.
+constexpr int kPref3 = 2;
 
 template <typename TY>
 __device__ __forceinline__ void tile_copy3(const TY* Y, int64_t f0, int nf, int I1, int ldy, float* dst);
@@ -597,6 +608,42 @@ __device__ __forceinline__ void tile_copy3<__nv_bfloat16>(const __nv_bfloat16* Y
   }
 }
 
+__device__ __forceinline__ void bf16_fetch3(const __nv_bfloat16* Y, int64_t f0, int nf, int I1,
+                                            uint4 (&v)[kPref3]) {
+  const int nvec = (nf * I1) / 8;
+  const uint4* src = reinterpret_cast<const uint4*>(Y + f0 * I1);
+#pragma unroll
+  for (int q = 0; q < kPref3; ++q) {
+    const int e8 = int(threadIdx.x) + q * kT3;
+    if (e8 < nvec) v[q] = src[e8];
+  }
+}
+
+__device__ __forceinline__ void bf16_store3(const __nv_bfloat16* Y, int64_t f0, int nf, int I1, int ldy,
+                                            const uint4 (&v)[kPref3], float* dst) {
+  const int tot = nf * I1, nvec = tot / 8;
+#pragma unroll
+  for (int q = 0; q < kPref3; ++q) {
+    const int e8 = int(threadIdx.x) + q * kT3;
+    if (e8 < nvec) {
+      int e = 8 * e8, f = e / I1, i = e - f * I1;
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v[q]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 x = __bfloat1622float2(h[j]);
+        dst[f * ldy + i] = x.x;
+        if (++i == I1) { i = 0; ++f; }
+        dst[f * ldy + i] = x.y;
+        if (++i == I1) { i = 0; ++f; }
+      }
+    }
+  }
+  for (int e = 8 * nvec + int(threadIdx.x); e < tot; e += kT3) {   // the last values of a ragged tile
+    const int f = e / I1;
+    dst[f * ldy + e - f * I1] = __bfloat162float(Y[f0 * I1 + e]);
+  }
+}
+
 template <typename TY, int PB>
 __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
   pdl_enter();
@@ -614,10 +661,14 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
   float* krs = A1t + size_t(Rp) * ldi;                          // TF x Rp    [f][r]
   float* krt = krs + size_t(TF) * Rp;                           // Rp x TF    [r][f]
   float* ts = krt + size_t(Rp) * TF;                            // kSeg3 x TF x Rp
-  float* loos = ts + size_t(kSeg3) * TF * Rp;                   // (N-1) x TF x Rp
+  float* loos = ts + size_t(p.fast ? 1 : kSeg3) * TF * Rp;       // (N-1) x TF x Rp
   float* Mn2 = loos + size_t(N - 1) * TF * Rp;                  // I_2 x R (if mn2_smem)
   const int64_t mn2 = p.mn2_smem ? d.I[1] * R : 0;
-  float* Yt0 = Mn2 + ((mn2 + 3) & ~int64_t(3));                 // 2 x TF x ldy
+  float* Af = Mn2 + ((mn2 + 3) & ~int64_t(3));                  // fast: rows of A^(2..N), [i][r]
+  // fast: partials of M_2..M_N, [i][r] (one writer per entry and tile, in a
+  // fixed order, so the sums do not depend on thread timing)
+  float* Mnh = Af + ((p.af_size + 3) & ~3);
+  float* Yt0 = Mnh + ((p.mh_size + 3) & ~3);                    // 2 x TF x ldy
   float* Yt1 = Yt0 + size_t(TF) * ldy;
   int* fidx = reinterpret_cast<int*>(Yt1 + size_t(TF) * ldy);   // TF x CP_MAX_N
   double* red = reinterpret_cast<double*>(
@@ -631,6 +682,17 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
     A1t[r * ldi + i] = v;
   }
   for (int64_t e = tid; e < mn2; e += kT3) Mn2[e] = 0.f;
+  if (p.fast) {
+    for (int e = tid; e < 2 * TF * ldy; e += kT3) Yt0[e] = 0.f;   // the padding of each row stays 0
+    for (int k = 1; k < N; ++k) {
+      const int Ik = int(d.I[k]);
+      for (int e = tid; e < Ik * Rp; e += kT3) {
+        const int i = e / Rp, r = e % Rp;
+        Af[p.afoff[k] + e] = (r < R) ? float(a[d.aoff[k] + i + int64_t(r) * Ik]) : 0.f;
+      }
+    }
+    for (int e = tid; e < p.mh_size; e += kT3) Mnh[e] = 0.f;
+  }
 
   const int64_t f_begin = int64_t(blockIdx.x) * p.fib_per_cta;
   const int64_t f_end = (f_begin + p.fib_per_cta < d.nfib) ? f_begin + p.fib_per_cta : d.nfib;
@@ -648,9 +710,20 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
       for (int v = 0; v < 4; ++v) accB[k][u][v] = 0.f;
   double e2_total = 0.0;
 
+  // bfloat16 with the fast layout: register prefetch (see bf16_fetch3)
+  constexpr bool kBf = sizeof(TY) == 2;
+  const bool pref = kBf && p.fast;
+  uint4 pv[kPref3];
   if (f_begin < f_end) {
     const int nf0 = int((f_end - f_begin) < TF ? (f_end - f_begin) : TF);
-    tile_copy3<TY>(Y, f_begin, nf0, I1, ldy, Yt0);
+    if (pref) {
+      if constexpr (kBf) {
+        bf16_fetch3(reinterpret_cast<const __nv_bfloat16*>(Y), f_begin, nf0, I1, pv);
+        bf16_store3(reinterpret_cast<const __nv_bfloat16*>(Y), f_begin, nf0, I1, ldy, pv, Yt0);
+      }
+    } else {
+      tile_copy3<TY>(Y, f_begin, nf0, I1, ldy, Yt0);
+    }
   }
   cp_async_commit();
   int buf = 0;
@@ -659,16 +732,35 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
     float* Yc = buf ? Yt1 : Yt0;
     float* Yn = buf ? Yt0 : Yt1;
     const int64_t f1 = f0 + TF;
-    if (f1 < f_end) tile_copy3<TY>(Y, f1, int((f_end - f1) < TF ? (f_end - f1) : TF), I1, ldy, Yn);
+    const int nf1 = f1 < f_end ? int((f_end - f1) < TF ? (f_end - f1) : TF) : 0;
+    if (pref) {
+      if constexpr (kBf) {
+        if (nf1 > 0) bf16_fetch3(reinterpret_cast<const __nv_bfloat16*>(Y), f1, nf1, I1, pv);
+      }
+    } else if (nf1 > 0) {
+      tile_copy3<TY>(Y, f1, nf1, I1, ldy, Yn);
+    }
     cp_async_commit();
     for (int f = tid; f < TF; f += kT3) {
-      int64_t rem = f0 + (f < nf ? f : 0);
+      if (p.fib32) {
+        uint32_t rem = uint32_t(f0 + (f < nf ? f : 0));
 #pragma unroll
-      for (int k = 1; k < CP_MAX_N; ++k)
-        if (k < N) {
-          fidx[f * CP_MAX_N + k] = int(rem % d.I[k]);
-          rem /= d.I[k];
-        }
+        for (int k = 1; k < CP_MAX_N; ++k)
+          if (k < N) {
+            const uint32_t Ik = uint32_t(d.I[k]);
+            const uint32_t qt = rem / Ik;
+            fidx[f * CP_MAX_N + k] = int(rem - qt * Ik);
+            rem = qt;
+          }
+      } else {
+        int64_t rem = f0 + (f < nf ? f : 0);
+#pragma unroll
+        for (int k = 1; k < CP_MAX_N; ++k)
+          if (k < N) {
+            fidx[f * CP_MAX_N + k] = int(rem % d.I[k]);
+            rem /= d.I[k];
+          }
+      }
     }
     __syncthreads();
     for (int e = tid; e < TF * Rp; e += kT3) {
@@ -677,7 +769,10 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
       float v[CP_MAX_N];
 #pragma unroll
       for (int k = 1; k < CP_MAX_N; ++k)
-        if (k < N) v[k] = ok ? float(a[d.aoff[k] + fidx[f * CP_MAX_N + k] + int64_t(r) * d.I[k]]) : 0.f;
+        if (k < N)
+          v[k] = !ok ? 0.f
+                     : (p.fast ? Af[p.afoff[k] + fidx[f * CP_MAX_N + k] * Rp + r]
+                               : float(a[d.aoff[k] + fidx[f * CP_MAX_N + k] + int64_t(r) * d.I[k]]));
       float kr = 1.f;
 #pragma unroll
       for (int k = 1; k < CP_MAX_N; ++k)
@@ -764,8 +859,32 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
         }
       }
     }
+    // ---- product A, fast layout: thread = (fibre f, 4 ranks), the whole row
+    // range, y read 16 bytes at a time (rows ldy = 4 mod 32 floats apart, so
+    // the 32 fibres of a warp hit every bank once per 8 lanes) ----
+    if (want_m && p.fast) {
+      const int nrq = Rp / 4;
+      for (int task = tid; task < TF * nrq; task += kT3) {
+        const int f = task % TF, rq = task / TF;
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        const float* yr = Yc + f * ldy;
+        for (int i = 0; i < ldi; i += 4) {
+          const float4 y4 = *reinterpret_cast<const float4*>(yr + i);
+          const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 a4 = *reinterpret_cast<const float4*>(A1s + (i + u) * Rp + rq * 4);
+            c0 = fmaf(yv[u], a4.x, c0);
+            c1 = fmaf(yv[u], a4.y, c1);
+            c2 = fmaf(yv[u], a4.z, c2);
+            c3 = fmaf(yv[u], a4.w, c3);
+          }
+        }
+        *reinterpret_cast<float4*>(ts + f * Rp + rq * 4) = make_float4(c0, c1, c2, c3);
+      }
+    }
     // ---- product A: t partials ----
-    if (want_m) {
+    if (want_m && !p.fast) {
       const int nfb8 = TF / 8, seg = (I1 + kSeg3 - 1) / kSeg3;
       for (int task = tid; task < nfb8 * ncb * kSeg3; task += kT3) {
         const int cb = task % ncb, fb = (task / ncb) % nfb8, sg = task / (ncb * nfb8);
@@ -794,15 +913,55 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
     }
     __syncthreads();
     if (want_m) {
-      for (int e = tid; e < TF * Rp; e += kT3) {
+      for (int e = tid; !p.fast && e < TF * Rp; e += kT3) {
         float sum = ts[e];
 #pragma unroll
         for (int sg = 1; sg < kSeg3; ++sg) sum += ts[size_t(sg) * TF * Rp + e];
         ts[e] = sum;
       }
       __syncthreads();
+      if (p.fast) {
+        // modes 2..N without atomics, one writer per partial entry, so the
+        // sums do not depend on thread timing.  The tile holds TF <= I_2
+        // consecutive fibres, so (i) their i_2 are distinct: mode 2 is one
+        // add per (fibre, rank); (ii) i_2 wraps at most once inside it, so
+        // for n >= 3 the tile is two runs [0, sw) and [sw, nf) of constant
+        // i_n, each summed by a warp.
+        for (int e = tid; e < nf * R; e += kT3) {
+          const int f = e / R, r = e % R;
+          Mnh[p.mhoff[1] + fidx[f * CP_MAX_N + 1] * R + r] += ts[f * Rp + r] * loos[f * Rp + r];
+        }
+        if (N > 2) {
+          // warp n - 2: lane = (rank, half of the tile's fibres), so the loads
+          // of a fibre's ranks are contiguous; the halves meet by a shuffle
+          const int i20 = fidx[1];
+          const int sw = (int(d.I[1]) - i20 < nf) ? int(d.I[1]) - i20 : nf;   // first fibre of the second run
+          const int warp = tid >> 5, lane = tid & 31;
+          const int nh = Rp <= 16 ? 2 : 1, r = lane % (32 / nh), h = lane / (32 / nh);
+          const int fh = (nf + nh - 1) / nh, fa = h * fh, fe = (fa + fh < nf) ? fa + fh : nf;
+          for (int n = 2 + warp; n < N; n += kT3 / 32) {
+            const float* lo = loos + size_t(n - 1) * TF * Rp;
+            float s0 = 0.f, s1 = 0.f;
+            if (r < Rp) {
+              for (int f = fa; f < fe; ++f) {
+                const float v = ts[f * Rp + r] * lo[f * Rp + r];
+                if (f < sw) s0 += v;
+                else s1 += v;
+              }
+            }
+            if (nh == 2) {
+              s0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+              s1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+            }
+            if (h == 0 && r < R) {
+              Mnh[p.mhoff[n] + fidx[n] * R + r] += s0;
+              if (sw < nf) Mnh[p.mhoff[n] + fidx[sw * CP_MAX_N + n] * R + r] += s1;
+            }
+          }
+        }
+      }
       // mode 2
-      if (p.mn2_smem) {
+      if (!p.fast && p.mn2_smem) {
         if (TF <= d.I[1]) {
           for (int e = tid; e < nf * R; e += kT3) {
             const int f = e / R, r = e % R;
@@ -817,7 +976,7 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
       }
       // modes >= 3 (and mode 2 without the shared partial): per (n, r), runs of equal i_n
       const int n_lo = p.mn2_smem ? 2 : 1;
-      for (int task = tid; task < (N - n_lo) * R; task += kT3) {
+      for (int task = tid; !p.fast && task < (N - n_lo) * R; task += kT3) {
         const int n = n_lo + task / R, r = task % R;
         int cur = fidx[n];
         float sacc = 0.f;
@@ -833,10 +992,16 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
         atomicAdd(&p.m[d.aoff[n] + cur + int64_t(r) * d.I[n]], double(sacc));
       }
     }
+    if (pref) {
+      if constexpr (kBf) {
+        if (nf1 > 0) bf16_store3(reinterpret_cast<const __nv_bfloat16*>(Y), f1, nf1, I1, ldy, pv, Yn);
+      }
+    }
     __syncthreads();
     buf ^= 1;
   }
   cp_async_wait<0>();
+  __syncthreads();
   if (want_m) {
 #pragma unroll
     for (int k = 0; k < PB; ++k) {
@@ -852,7 +1017,15 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
           }
       }
     }
-    if (p.mn2_smem) {
+    if (p.fast) {
+      for (int n = 1; n < N; ++n) {
+        const int In = int(d.I[n]);
+        for (int e = tid; e < In * R; e += kT3) {
+          const int i = e % In, r = e / In;
+          atomicAdd(&p.m[d.aoff[n] + i + int64_t(r) * In], double(Mnh[p.mhoff[n] + i * R + r]));
+        }
+      }
+    } else if (p.mn2_smem) {
       const int I2 = int(d.I[1]);
       for (int e = tid; e < I2 * R; e += kT3) {
         const int i = e % I2, r = e / I2;
@@ -866,9 +1039,13 @@ __global__ void __launch_bounds__(kT3) k_mttkrp3(P3 p) {
   }
 }
 
-static size_t smem3(const Dims& d, int TF, int ldy, int Rp, int ldi, int mn2_smem) {
-  size_t f = size_t(ldi) * Rp * 2 + size_t(TF) * Rp * 2 + size_t(kSeg3) * TF * Rp + size_t(d.N - 1) * TF * Rp;
+static size_t smem3(const Dims& d, int TF, int ldy, int Rp, int ldi, int mn2_smem, int af_size = 0,
+                    int mh_size = 0) {
+  const bool fast = af_size > 0;
+  size_t f = size_t(ldi) * Rp * 2 + size_t(TF) * Rp * 2 + size_t(fast ? 1 : kSeg3) * TF * Rp +
+             size_t(d.N - 1) * TF * Rp;
   if (mn2_smem) f += (size_t(d.I[1]) * d.R + 3) & ~size_t(3);
+  f += ((size_t(af_size) + 3) & ~size_t(3)) + ((size_t(mh_size) + 3) & ~size_t(3));
   f += 2 * size_t(TF) * ldy;
   return f * 4 + size_t(TF) * CP_MAX_N * 4 + 16 + kT3 * 8 + 16;
 }
@@ -907,16 +1084,40 @@ int launch_mttkrp3(const Dims& d, const void* Y, const double* a, double* m, dou
   int ldy = (I1 + 3) / 4 * 4;
   while (ldy % 32 != 4) ldy += 4;
   const size_t max_smem = 200 * 1024;
-  int mn2_smem = 1;
-  size_t smem = smem3(d, TF, ldy, Rp, ldi, 1);
-  if (smem > max_smem || d.I[1] * d.R > 16384) {
+  // the fast layout: factor rows of modes 2..N (float, I_k x Rp) and the
+  // partials of M_2..M_N (I_n x R) in shared memory; bfloat16 tiles then go
+  // through the register prefetch, which holds at most kPref3 * kT3 * 8 values
+  int af_size = 0, mh_size = 0;
+  int afoff[CP_MAX_N] = {0}, mhoff[CP_MAX_N] = {0};
+  for (int k = 1; k < d.N; ++k) {
+    afoff[k] = af_size;
+    mhoff[k] = mh_size;
+    af_size += int(d.I[k]) * Rp;
+    mh_size += int(d.I[k]) * d.R;
+  }
+  // the fast layout also needs tiles of at most I_2 fibres (see the mode sums)
+  int fast = (af_size + mh_size <= 24576 && d.I[1] >= 8) ? 1 : 0;
+  const int TF_all = TF;
+  if (fast && TF > d.I[1]) TF = int(d.I[1]) & ~7;
+  if (fast && d.y_dtype == CP_BF16 && int64_t(TF) * I1 > int64_t(kPref3) * kT3 * 8) fast = 0;
+  if (fast && d.y_dtype == CP_BF16 && (reinterpret_cast<uintptr_t>(Y) & 15) != 0) fast = 0;   // 16-byte loads
+  if (!fast) TF = TF_all;
+  int mn2_smem = fast ? 0 : 1;
+  size_t smem = fast ? smem3(d, TF, ldy, Rp, ldi, 0, af_size, mh_size) : smem3(d, TF, ldy, Rp, ldi, 1);
+  if (fast && smem > max_smem) {
+    fast = 0;
+    mn2_smem = 1;
+    TF = TF_all;
+    smem = smem3(d, TF, ldy, Rp, ldi, 1);
+  }
+  if (!fast && (smem > max_smem || d.I[1] * d.R > 16384)) {
     mn2_smem = 0;
     smem = smem3(d, TF, ldy, Rp, ldi, 0);
   }
   while (smem > max_smem && TF > 8) {
     TF = (TF / 2) & ~7;
     if (TF < 8) TF = 8;
-    smem = smem3(d, TF, ldy, Rp, ldi, mn2_smem);
+    smem = fast ? smem3(d, TF, ldy, Rp, ldi, 0, af_size, mh_size) : smem3(d, TF, ldy, Rp, ldi, mn2_smem);
   }
   if (smem > max_smem) return CP_EINVAL;
   int per_sm = int((228 * 1024) / (smem + 1024));
@@ -944,6 +1145,14 @@ int launch_mttkrp3(const Dims& d, const void* Y, const double* a, double* m, dou
   p.FS = FS;
   p.mn2_smem = mn2_smem;
   p.grad = grad;
+  p.fast = fast;
+  p.fib32 = (d.nfib + TF < int64_t(0xFFFFFFFFll)) ? 1 : 0;
+  for (int k = 0; k < CP_MAX_N; ++k) {
+    p.afoff[k] = fast ? afoff[k] : 0;
+    p.mhoff[k] = fast ? mhoff[k] : 0;
+  }
+  p.af_size = fast ? af_size : 0;
+  p.mh_size = fast ? mh_size : 0;
   grid = (d.nfib + p.fib_per_cta - 1) / p.fib_per_cta;
   if (d.y_dtype == CP_F32) {
     switch (PB) {
