@@ -1088,7 +1088,7 @@ def run_reference(args):
         return
     from oracle import cp_oracle as O
     from paper_1205_2584_gb300 import synth
-    prob = synth.config2(args.seed, DIMS, dtype="bf16x2")
+    prob = synth.config2(args.seed, DIMS, dtype="f32")
     # warm-up iterations, then K timed LM iterations continuing from there
     w = O.lm_fit(prob.Y, prob.init, mu0=None, max_iter=max(1, args.warmup), tol=0.0)
     t0 = time.perf_counter()
@@ -1100,7 +1100,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R,
-                      "tensor_dtype": "bf16x2 values (hi + lo) in float64, f64 math"},
+                      "tensor_dtype": "f32 (the float32 tensor values in float64, f64 math)"},
            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": oracle_threads(), "kind": "oracle",
                             "sample": f"{len(times)} consecutive LM iterations from the seeded start"},
            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
