@@ -48,7 +48,7 @@ namespace cpdgn {
 
 namespace {
 
-constexpr int kTcThreads = 192;                  // warps 0-3 SIMT, 4 TMA, 5 MMA
+constexpr int kTcThreads = 320;                  // warps 0-3 and 6-9 SIMT (two groups), 4 TMA, 5 MMA
 constexpr int kSlots = 4;                        // TMA ring (16 KB boxes)
 constexpr int kBoxBytes = 32 * 128 * 4;          // 32 i1 x 128 i2 float32
 constexpr int kYpcBytes = 128 * 128 * 2;         // one bf16 piece of the tensor tile
@@ -139,14 +139,15 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[32]) {
   return v[0];
 }
 
-// Named barrier 1 over the 128 SIMT threads (warps 0-3); every SIMT thread
-// reaches each call, so no decision that precedes one may differ per thread.
-__device__ __forceinline__ void simt_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-// The same barrier as a vote: true iff `v` holds in all 128 SIMT threads.
+// Named barrier 1 over the 256 SIMT threads of the float32 pass (warps 0-3
+// and 6-9); every SIMT thread reaches each call, so no decision that precedes
+// one may differ per thread.
+__device__ __forceinline__ void simt_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// The same barrier as a vote: true iff `v` holds in all 256 SIMT threads.
 __device__ __forceinline__ bool simt_all(bool v) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}"
       : "=r"(r)
       : "r"(uint32_t(v))
       : "memory");
@@ -177,6 +178,76 @@ __device__ __forceinline__ void build_w(unsigned char* wbuf, const float (&a2)[3
   }
 }
 
+// Half-row forms for the float32 pass, whose two SIMT warp groups each take
+// 16 of the 32 rank columns (group g: ranks 16 g .. 16 g + 15).
+__device__ __forceinline__ void build_a1_half(const double* a, int64_t I1, int R, int i1, int row, int g,
+                                              unsigned char* apc) {
+  float v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int r = 16 * g + j;
+    v[j] = (i1 < I1 && r < R) ? float(a[i1 + I1 * r]) : 0.f;
+  }
+#pragma unroll
+  for (int rh = 0; rh < 2; ++rh) {
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      __nv_bfloat16 x0[2], x1[2], x2[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) split3(v[rh * 8 + h * 2 + q], x0[q], x1[q], x2[q]);
+      w0[h] = pack2(x0[0], x0[1]);
+      w1[h] = pack2(x1[0], x1[1]);
+      w2[h] = pack2(x2[0], x2[1]);
+    }
+    const int c = 16 * g + rh * 8;
+    *reinterpret_cast<uint4*>(apc + coff(row, c, kArow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    *reinterpret_cast<uint4*>(apc + coff(row, 32 + c, kArow)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4*>(apc + coff(row, 64 + c, kArow)) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  }
+}
+
+__device__ __forceinline__ void build_w_half(unsigned char* wbuf, const float (&a2)[16], const float* a3, int row,
+                                             int g) {
+#pragma unroll
+  for (int rh = 0; rh < 2; ++rh) {
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      __nv_bfloat16 x0[2], x1[2], x2[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int j = rh * 8 + h * 2 + e;
+        split3(a2[j] * a3[16 * g + j], x0[e], x1[e], x2[e]);
+      }
+      w0[h] = pack2(x0[0], x0[1]);
+      w1[h] = pack2(x1[0], x1[1]);
+      w2[h] = pack2(x2[0], x2[1]);
+    }
+    const int c = 16 * g + rh * 8;
+    *reinterpret_cast<uint4*>(wbuf + coff(row, c, kWrow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    *reinterpret_cast<uint4*>(wbuf + coff(row, 32 + c, kWrow)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4*>(wbuf + coff(row, 64 + c, kWrow)) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  }
+}
+
+// lane l returns the sum over the warp of v[l % 16] (recursive halving over
+// the 16 values, then the two half-warps added)
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 8; off >= 1; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const float send = up ? v[i] : v[i + off];
+      const float keep = up ? v[i + off] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_constant__ CUtensorMap tmap, TcParams p) {
   pdl_enter();
   if (p.skip && *p.skip) return;
@@ -184,7 +255,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
   __shared__ uint64_t bar_full[kSlots], bar_empty[kSlots];
   __shared__ uint64_t bar_p[2], bar_mma, bar_ypc, bar_w[2];
   __shared__ uint32_t tbase_s;
-  __shared__ float red[4][32];
+  __shared__ float red[10][32];                    // per SIMT warp (indexed by warp number)
   __shared__ float a3s[3][32];
   __shared__ int abort_s;
 
@@ -216,9 +287,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
     tc::mbar_init(&bar_p[0], 1);
     tc::mbar_init(&bar_p[1], 1);
     tc::mbar_init(&bar_mma, 1);
-    tc::mbar_init(&bar_ypc, 4);
-    tc::mbar_init(&bar_w[0], 4);
-    tc::mbar_init(&bar_w[1], 4);
+    tc::mbar_init(&bar_ypc, 8);                    // every SIMT warp of both groups
+    tc::mbar_init(&bar_w[0], 8);
+    tc::mbar_init(&bar_w[1], 8);
     tc::fence_barrier_init();
     abort_s = 0;
   }
@@ -226,17 +297,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
     tc::tmem_alloc(&tbase_s, kTmemCols);
     tc::tmem_relinquish();
   }
-  float a2[32];
-  if (warp < 4) {
+  // SIMT groups: warps 0-3 (group 0) and 6-9 (group 1); a SIMT thread owns
+  // row `srow` (TMEM lane) and the ranks 16 sg .. 16 sg + 15 of it, and
+  // the tensor boxes 2 sg, 2 sg + 1 of every step
+  const bool simt = warp < 4 || warp >= 6;
+  const int sg = warp >= 6 ? 1 : 0;
+  const int srow = 32 * (warp & 3) + lane;
+  float a2[16];
+  if (simt) {
     // zero the bf16 tensor pieces (columns past the valid i1 stay zero)
     uint4* z = reinterpret_cast<uint4*>(ypc);
-    for (int e = tid; e < 2 * kYpcBytes / 16; e += 128) z[e] = make_uint4(0, 0, 0, 0);
+    for (int e = srow + 128 * sg; e < 2 * kYpcBytes / 16; e += 256) z[e] = make_uint4(0, 0, 0, 0);
     // A1 chunk pieces, row t = i1 - i1_0, piece-interleaved (see kArow)
-    build_a1_row(p.a, p.I1, R, i1_0 + tid, tid, apc);
-    const int i2 = i2_0 + tid;
+    build_a1_half(p.a, p.I1, R, i1_0 + srow, srow, sg, apc);
+    const int i2 = i2_0 + srow;
     const double* A2 = p.a + int64_t(p.I1) * R;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) a2[r] = (i2 < p.I2 && r < R) ? float(A2[i2 + int64_t(p.I2) * r]) : 0.f;
+    for (int j = 0; j < 16; ++j) {
+      const int r = 16 * sg + j;
+      a2[j] = (i2 < p.I2 && r < R) ? float(A2[i2 + int64_t(p.I2) * r]) : 0.f;
+    }
     if (tid < 32) {
       a3s[0][tid] = (tid < R) ? float(A3[s0 + int64_t(p.I3) * tid]) : 0.f;
       if (nsteps > 1) a3s[1][tid] = (tid < R) ? float(A3[s0 + 1 + int64_t(p.I3) * tid]) : 0.f;
@@ -328,55 +408,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
       tc::mbar_wait(&bar_mma, (nsteps - 1) & 1, 200000000ull);
     }
   } else {
-    // ---------------- SIMT warps 0-3 (TMEM lanes 32 w .. 32 w + 31) ----------------
-    const uint32_t lane_base = uint32_t(warp * 32) << 16;
+    // ---------------- SIMT warps 0-3 and 6-9 (TMEM lanes 32 (w % 4) ..) ----------------
+    const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
     const uint32_t tl = tb + lane_base;
+    const uint32_t hc = 16 * sg;                   // this group's first rank column
     {
-      float z[32];
+      float z[16];
 #pragma unroll
-      for (int r = 0; r < 32; ++r) z[r] = 0.f;
-      tc::tmem_st32(tl + kColA2, a2);
-      tc::tmem_st32(tl + kColM2, z);
+      for (int j = 0; j < 16; ++j) z[j] = 0.f;
+      tc::tmem_st16(tl + kColA2 + hc, a2);
+      tc::tmem_st16(tl + kColM2 + hc, z);
     }
     double racc = 0.0;
     bool ok = true;
-    auto load_a2 = [&](float (&v)[32]) { tc::tmem_ld32(tl + kColA2, v); };
     auto make_w = [&](int st) {
-      float a2r[32];
-      load_a2(a2r);
-      build_w(wpc + (st & 1) * kWpcBytes, a2r, a3s[st % 3], tid);
+      float a2r[16];
+      tc::tmem_ld16(tl + kColA2 + hc, a2r);
+      build_w_half(wpc + (st & 1) * kWpcBytes, a2r, a3s[st % 3], srow, sg);
       tc::fence_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bar_w[st & 1]);
     };
-    // V epilogue: M2 (+)= V A3(i3, :) in TMEM, M3(i3, :) = sum_f V A2 (atomics)
+    // V epilogue: M2 (+)= V A3(i3, :) in TMEM, M3(i3, :) = sum_f V A2 (atomics);
+    // each group takes its 16 ranks
     auto v_epilogue = [&](int st) {
-      float v[32], t[32];
-      tc::tmem_ld32(tl + kColV, v);
+      float v[16], t[16];
+      tc::tmem_ld16(tl + kColV + hc, v);
 #pragma unroll
       for (int q = 1; q < 3; ++q) {
-        tc::tmem_ld32(tl + kColV + 32 * q, t);
+        tc::tmem_ld16(tl + kColV + 32 * q + hc, t);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] += t[r];
+        for (int j = 0; j < 16; ++j) v[j] += t[j];
       }
       const float* a3 = a3s[st % 3];
-      tc::tmem_ld32(tl + kColM2, t);
+      tc::tmem_ld16(tl + kColM2 + hc, t);
 #pragma unroll
-      for (int r = 0; r < 32; ++r) t[r] = fmaf(v[r], a3[r], t[r]);
-      tc::tmem_st32(tl + kColM2, t);
-      load_a2(t);
+      for (int j = 0; j < 16; ++j) t[j] = fmaf(v[j], a3[hc + j], t[j]);
+      tc::tmem_st16(tl + kColM2 + hc, t);
+      tc::tmem_ld16(tl + kColA2 + hc, t);
 #pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] *= t[r];
-      const float sum = warp_transpose_sum(v);
+      for (int j = 0; j < 16; ++j) v[j] *= t[j];
+      const float sum = warp_transpose_sum16(v);
       red[warp][lane] = sum;
       simt_sync();
-      if (tid < R && p.m) {
-        const float tt = red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
-        atomicAdd(p.m + int64_t(p.I1 + p.I2) * R + (s0 + st) + int64_t(p.I3) * tid, double(tt));
+      if (lane < 16 && (warp & 3) == 0) {          // warp 0: ranks 0-15, warp 8: ranks 16-31
+        const int r = int(hc) + lane;
+        const int w0 = sg ? 6 : 0;
+        if (r < R && p.m) {
+          const float tt = red[w0][lane] + red[w0 + 1][lane] + red[w0 + 2][lane] + red[w0 + 3][lane];
+          atomicAdd(p.m + int64_t(p.I1 + p.I2) * R + (s0 + st) + int64_t(p.I3) * r, double(tt));
+        }
       }
     };
     make_w(0);
 
+    // boxes of this group: 2 sg, 2 sg + 1 (those below nbox)
+    const int kb0 = 2 * sg, kb1 = (2 * sg + 2 < nbox) ? 2 * sg + 2 : nbox;
     for (int st = 0; st < nsteps; ++st) {
       // prefetch A3 row of step st + 2 (stored once V epilogue st - 1 is done)
       float a3next = 0.f;
@@ -402,22 +489,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
       const uint32_t pcol = tl + kColP + (st & 1) * 128;
       bool wok = true;
       uint32_t phr[32];
-      tc::tmem_ld32_async(pcol, phr);
-      for (int k = 0; k < nbox; ++k) {
+      if (kb0 < kb1) tc::tmem_ld32_async(pcol + 32 * kb0, phr);
+      for (int k = kb0; k < kb1; ++k) {
         const int g = st * nbox + k;
         const int slot = g % kSlots;
         tc::tmem_wait_ld();
         float ph[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) ph[j] = __uint_as_float(phr[j]);
-        if (k + 1 < nbox) tc::tmem_ld32_async(pcol + 32 * (k + 1), phr);
+        if (k + 1 < kb1) tc::tmem_ld32_async(pcol + 32 * (k + 1), phr);
         wok = __all_sync(0xffffffffu, tc::mbar_wait(&bar_full[slot], (g / kSlots) & 1));
         if (!wok) break;
-        const unsigned char* row = stage + slot * kBoxBytes + tid * 128;
+        const unsigned char* row = stage + slot * kBoxBytes + srow * 128;
         float y[32];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const float4 v = *reinterpret_cast<const float4*>(row + ((j ^ (tid & 7)) << 4));
+          const float4 v = *reinterpret_cast<const float4*>(row + ((j ^ (srow & 7)) << 4));
           y[4 * j] = v.x;
           y[4 * j + 1] = v.y;
           y[4 * j + 2] = v.z;
@@ -445,7 +532,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
             h0[h] = *reinterpret_cast<const uint32_t*>(&p0);
             h1[h] = *reinterpret_cast<const uint32_t*>(&p1);
           }
-          const uint32_t o = coff(tid, 32 * k + 8 * g8, 2048);
+          const uint32_t o = coff(srow, 32 * k + 8 * g8, 2048);
           *reinterpret_cast<uint4*>(ypc + o) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
           *reinterpret_cast<uint4*>(ypc + kYpcBytes + o) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
         }
@@ -465,27 +552,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mttkrp_tc(const __grid_consta
       tc::tc_fence_after();
       v_epilogue(nsteps - 1);
       // M1 flush: lanes are i1 of the chunk; the three column blocks summed
-      float v[32], t[32];
-      tc::tmem_ld32(tl + kColM1, v);
+      float v[16], t[16];
+      tc::tmem_ld16(tl + kColM1 + hc, v);
 #pragma unroll
       for (int q = 1; q < 3; ++q) {
-        tc::tmem_ld32(tl + kColM1 + 32 * q, t);
+        tc::tmem_ld16(tl + kColM1 + 32 * q + hc, t);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] += t[r];
+        for (int j = 0; j < 16; ++j) v[j] += t[j];
       }
-      tc::tmem_ld32(tl + kColM2, t);
+      tc::tmem_ld16(tl + kColM2 + hc, t);
       if (p.m) {
-        const int i1 = i1_0 + tid;
+        const int i1 = i1_0 + srow;
         if (i1 < p.I1) {
 #pragma unroll
-          for (int r = 0; r < 32; ++r)
-            if (r < R) atomicAdd(p.m + i1 + int64_t(p.I1) * r, double(v[r]));
+          for (int j = 0; j < 16; ++j)
+            if (int(hc) + j < R) atomicAdd(p.m + i1 + int64_t(p.I1) * (int(hc) + j), double(v[j]));
         }
-        const int i2 = i2_0 + tid;
+        const int i2 = i2_0 + srow;
         if (i2 < p.I2) {
 #pragma unroll
-          for (int r = 0; r < 32; ++r)
-            if (r < R) atomicAdd(p.m + int64_t(p.I1) * R + i2 + int64_t(p.I2) * r, double(t[r]));
+          for (int j = 0; j < 16; ++j)
+            if (int(hc) + j < R)
+              atomicAdd(p.m + int64_t(p.I1) * R + i2 + int64_t(p.I2) * (int(hc) + j), double(t[j]));
         }
       }
       if (p.resid2) {
