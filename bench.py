@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 256 << 20
 # since its counters were taken.
 TRAFFIC_TC3_200 = 32.299520e6          # k_mttkrp_tc3, 200^3 R=20, two-plane tensor
 TRAFFIC_TC3_512 = 537.898752e6 + 2.792192e6   # k_mttkrp_tc3, 512^3 R=32
-TRAFFIC_TC_200 = None                  # k_mttkrp_tc, 200^3 R=20, float32 tensor
+TRAFFIC_TC_200 = 32.286208e6           # k_mttkrp_tc, 200^3 R=20, float32 tensor
 # summed over the kernels of one float32 core inverse (n = 1200), every kernel
 # with cold caches under ncu (bytes)
 GJ_TRAFFIC = 95.024128e6
