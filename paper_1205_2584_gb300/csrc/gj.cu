@@ -44,9 +44,9 @@ constexpr int GJH = 32;           // width of a half tile
 constexpr int GJTH = 64;          // threads of a 64 x 32 half-tile CTA: 8 x 8 threads, 8 x 4 entries each
 constexpr int GJP = GJB + 4;      // padded row length in shared memory (keeps float4 alignment)
 // shared memory reserved by k_gj_pivot_next on top of its static arrays
-// (about 53 KB): with it the CTA holds about 221 KB of the SM's 228 KB, so no
-// half-tile CTA (about 27 KB) fits beside it; the sum stays under the 227 KB
-// per-block limit
+// (56 KB): with it the CTA holds 224 KB of the SM's 228 KB, so no half-tile
+// CTA (about 27 KB) fits beside it; the sum stays under the 227 KB per-block
+// limit
 constexpr int kPivotReserve = 168 * 1024;
 
 // Reciprocal of a pivot.  The float32 inverse only preconditions the float64
@@ -461,35 +461,19 @@ __device__ __forceinline__ uint32_t ut_off(int row, int col) {
   return uint32_t((row >> 3) * 1024 + (col >> 3) * 128 + (row & 7) * 16 + (col & 7) * 2);
 }
 
-__device__ __forceinline__ uint32_t ut_pack(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return uint32_t(__bfloat16_as_ushort(lo)) | (uint32_t(__bfloat16_as_ushort(hi)) << 16);
-}
-
 // the three bfloat16 pieces of 32 values of operand row `row`, inner index
-// l0 .. l0 + 31
+// l0 .. l0 + 31 (pieces PS bytes apart)
+template <int PS = kUtPiece>
 __device__ __forceinline__ void ut_store_half(unsigned char* base, int row, int l0, const float (&v)[32]) {
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      __nv_bfloat16 x0[2], x1[2], x2[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float x = v[8 * g + 2 * h + q];
-        x0[q] = __float2bfloat16_rn(x);
-        const float r1 = x - __bfloat162float(x0[q]);
-        x1[q] = __float2bfloat16_rn(r1);
-        x2[q] = __float2bfloat16_rn(r1 - __bfloat162float(x1[q]));
-      }
-      w0[h] = ut_pack(x0[0], x0[1]);
-      w1[h] = ut_pack(x1[0], x1[1]);
-      w2[h] = ut_pack(x2[0], x2[1]);
-    }
+    for (int h = 0; h < 4; ++h) tc::split3x2(v[8 * g + 2 * h], v[8 * g + 2 * h + 1], w0[h], w1[h], w2[h]);
     const uint32_t o = ut_off(row, l0 + 8 * g);
     *reinterpret_cast<uint4*>(base + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-    *reinterpret_cast<uint4*>(base + kUtPiece + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    *reinterpret_cast<uint4*>(base + 2 * kUtPiece + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+    *reinterpret_cast<uint4*>(base + PS + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4*>(base + 2 * PS + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
   }
 }
 
@@ -731,19 +715,31 @@ __global__ void __launch_bounds__(GJTH) k_gj_identity(const T* A, T* B, int64_t 
 // is inverted by one 128-thread CTA that keeps the block in registers (4 x 8
 // entries per thread); an elimination step broadcasts the pivot row (two
 // float4 per owning thread) and column (one float4) through shared memory,
-// double-buffered, so one barrier per step.  A step is about 170 cycles of
-// dependent latency (store, barrier, load, reciprocal, multiply-add), so a
-// 64 x 64 inverse takes about 6 us; the 256-thread 4 x 4 layout took about
-// 240 cycles a step, its extra instructions per step lying on the chain.
-// For sweep k + 1 the same CTA first forms its pivot tile
-// X = A[k+1,k+1] - A[k+1,k] (P_k^{-1} A[k,k+1]) from sweep k's input, so it
-// runs concurrently with sweep k's row panel and update.
+// double-buffered, so one barrier per step.  A step is about 160 cycles of
+// dependent latency (store, barrier, load, reciprocal, multiply-add): 10.4K
+// cycles a tile, measured.  Eliminating four pivots per barrier (each thread
+// inverting the 4 x 4 pivot block itself, then a rank-4 update) took 13.4K
+// cycles, and the 256-thread 4 x 4 layout about 240 cycles a step: the extra
+// instructions lie on the chain.  For sweep k + 1 the pivot tile
+// X = A[k+1,k+1] - A[k+1,k] (P_k^{-1} A[k,k+1]) is first formed from sweep
+// k's input, so that it is inverted concurrently with sweep k's row panel
+// and update.
 // ---------------------------------------------------------------------------
+// Barrier of the 128 pivot threads: the whole CTA, or (NB) named barrier 1
+// over warps 0-3 when the pivot runs inside a larger CTA whose other warps
+// have left.
+template <bool NB>
+__device__ __forceinline__ void gj_sync() {
+  if constexpr (NB) asm volatile("bar.sync 1, 128;\n" ::: "memory");
+  else __syncthreads();
+}
+
 // All 64 steps run, in groups of 8 so that the row and column a step reads
 // sit at compile-time offsets of the owning threads' registers.  Rows and
 // columns beyond kb hold the identity (pad_identity), and a step on such a
 // unit row/column leaves the tile unchanged; only the first kb pivots are
 // checked.
+template <bool NB>
 __device__ void gj_invert_tile(float (&x)[4][8], int kb, float (*prow)[GJB], float (*pcol)[GJB], int* bad) {
   __shared__ float pv[GJB];                                    // pivots, checked at the end
   const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
@@ -757,7 +753,7 @@ __device__ void gj_invert_tile(float (&x)[4][8], int kb, float (*prow)[GJB], flo
         *reinterpret_cast<float4*>(&prow[par][8 * bj + 4]) = make_float4(x[lr][4], x[lr][5], x[lr][6], x[lr][7]);
       }
       if (ocol) *reinterpret_cast<float4*>(&pcol[par][4 * bi]) = make_float4(x[0][q], x[1][q], x[2][q], x[3][q]);
-      __syncthreads();
+      gj_sync<NB>();
       const float piv = prow[par][p];
       if (threadIdx.x == 0) pv[p] = piv;
       const float dinv = recip(piv);
@@ -782,9 +778,9 @@ __device__ void gj_invert_tile(float (&x)[4][8], int kb, float (*prow)[GJB], flo
     }
   }
   // check the recorded pivots once, after the elimination
-  __syncthreads();
+  gj_sync<NB>();
   if (threadIdx.x < kb && !(pv[threadIdx.x] > 0.f && isfinite(pv[threadIdx.x]))) atomicMin(bad, threadIdx.x + 1);
-  __syncthreads();
+  gj_sync<NB>();
 }
 
 // rows/columns of a partial pivot tile beyond kb become the identity
@@ -799,14 +795,16 @@ __device__ __forceinline__ void pad_identity(float (&x)[4][8], int kb) {
 
 // Invert x (pivot tile kk) and write P^{-1} to Pinv (64 x 64) and into tile
 // (kk, kk) of D.
+// (D == nullptr: Pinv only.)
+template <bool NB>
 __device__ void pivot_store(float (&x)[4][8], int64_t n, int kk, int kb, float* Pinv, float* D, int* info,
                             float (*prow)[GJB], float (*pcol)[GJB], int* bad) {
   if (threadIdx.x == 0) *bad = GJB + 1;
-  __syncthreads();
-  gj_invert_tile(x, kb, prow, pcol, bad);
+  gj_sync<NB>();
+  gj_invert_tile<NB>(x, kb, prow, pcol, bad);
   if (threadIdx.x == 0 && *bad <= GJB && info) atomicCAS(info, 0, kk * GJB + *bad);
   store_block(x, Pinv, GJB, 0, 0);
-  store_block(x, D, n, int64_t(kk) * GJB, int64_t(kk) * GJB);
+  if (D) store_block(x, D, n, int64_t(kk) * GJB, int64_t(kk) * GJB);
 }
 
 // Pivot of sweep k (tile (k, k) of A as it stands); P^{-1} also into D's tile.
@@ -821,7 +819,7 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot(const T* A, T* D, int64_t n, i
   float x[4][8];
   load_block(A, n, int64_t(k) * GJB, int64_t(k) * GJB, x);
   pad_identity(x, kb);
-  pivot_store(x, n, k, kb, Pinv, D, info, prow, pcol, &bad);
+  pivot_store<false>(x, n, k, kb, Pinv, D, info, prow, pcol, &bad);
 }
 
 // x += SGN L R with L = Lc (64 x 64, stored by columns: Lc[l][r] = L(r, l))
@@ -876,20 +874,17 @@ __device__ __forceinline__ void copy_cols_async(const float* A, int64_t n, int64
 
 // Pivot of sweep k + 1 during sweep k, from sweep k's input A and pivot
 // inverse Pinv alone: X = A[k+1,k+1] - A[k+1,k] (P^{-1} A[k,k+1]), inverted;
-// X^{-1} goes to Pinv_next and into A's tile (k+1, k+1), which sweep k + 1
-// writes into and which no kernel of sweep k reads.  The three operand tiles
-// are fetched at once (ASYNC, n % 4 == 0: cp.async, 16 bytes a copy; else
-// scalar loads), all stored by columns, before the first product.  Launched
+// X^{-1} goes to Pinv_next and (D != nullptr) into D's tile (k+1, k+1).  The
+// three operand tiles are fetched at once (ASYNC, n % 4 == 0: cp.async, 16
+// bytes a copy; else scalar loads), all stored by columns, before the first
+// product.  k_gj_pivot_next runs it on a side stream with D = A (the tile
+// that sweep k + 1 writes into and that no kernel of sweep k reads), launched
 // with kPivotReserve bytes of dynamic shared memory (unused: it keeps the
 // tile CTAs of the concurrent sweep off this SM).
 template <typename T, bool ASYNC>
-__global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, const T* Pinv, T* Pinv_next,
-                                                       int* info, const int* skip) {
-  pdl_enter();
-  if (skip && *skip) return;
-  __shared__ __align__(16) float Ls[GJB][GJP], Rc[GJB][GJP], L2s[GJB][GJP];
-  __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
-  __shared__ int bad;
+__device__ __forceinline__ void pivot_next_body(const T* A, int64_t n, int k, const T* Pinv, T* Pinv_next, int* info,
+                                                float (*Ls)[GJP], float (*Rc)[GJP], float (*L2s)[GJP],
+                                                float (*prow)[GJB], float (*pcol)[GJB], int* bad, T* D) {
   const int k1 = k + 1;
   const int kb = int((n - int64_t(k1) * GJB) < GJB ? (n - int64_t(k1) * GJB) : GJB);
   const int64_t o = int64_t(k) * GJB, o1 = int64_t(k1) * GJB;
@@ -917,7 +912,357 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, c
   __syncthreads();
   tile_fma_cc<-1>(L2s, Rc, x);                       // x = A[k+1,k+1] - A[k+1,k] t
   pad_identity(x, kb);
-  pivot_store(x, n, k1, kb, Pinv_next, A, info, prow, pcol, &bad);
+  pivot_store<false>(x, n, k1, kb, Pinv_next, D, info, prow, pcol, bad);
+}
+
+template <typename T, bool ASYNC>
+__global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, const T* Pinv, T* Pinv_next,
+                                                       int* info, const int* skip) {
+  pdl_enter();
+  if (skip && *skip) return;
+  __shared__ __align__(16) float Ls[GJB][GJP], Rc[GJB][GJP], L2s[GJB][GJP];
+  __shared__ __align__(16) float prow[2][GJB], pcol[2][GJB];
+  __shared__ int bad;
+  pivot_next_body<T, ASYNC>(A, n, k, Pinv, Pinv_next, info, Ls, Rc, L2s, prow, pcol, &bad, A);
+}
+
+// x += SGN L R on a 64 x 64 tile with 256 threads: thread (bi, bj) =
+// (tid % 16, tid / 16) owns rows 4 bi .. + 3 and columns 4 bj .. + 3; L and
+// R stored by columns (Lc[l][r] = L(r, l), Rc[c][l] = R(l, c)).  Four inner
+// steps per iteration: four float4 of L and four of R for 64 multiply-adds.
+template <int SGN>
+__device__ __forceinline__ void tile_fma_cc4(const float (*Lc)[GJP], const float (*Rc)[GJP], float (&x)[4][4]) {
+  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
+#pragma unroll 4
+  for (int l = 0; l < GJB; l += 4) {
+    float a[4][4], b[4][4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const float4 t = *reinterpret_cast<const float4*>(&Lc[l + w][4 * bi]);
+      a[w][0] = SGN * t.x;
+      a[w][1] = SGN * t.y;
+      a[w][2] = SGN * t.z;
+      a[w][3] = SGN * t.w;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float4 t = *reinterpret_cast<const float4*>(&Rc[4 * bj + v][l]);
+      b[v][0] = t.x;
+      b[v][1] = t.y;
+      b[v][2] = t.z;
+      b[v][3] = t.w;
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[u][v] = fmaf(a[w][u], b[v][w], x[u][v]);
+  }
+}
+
+// The pivot of sweep k + 1 as pivot_next_body forms it (n % 4 == 0), inside
+// a 256-thread CTA: the two products on all eight warps (two warps per
+// scheduler hide the shared-memory latency that bounds the products of the
+// 128-thread form: about 3.6K and 4.0K cycles there), then X passes through
+// shared memory to warps 0-3, which invert it (named barrier 1) and write
+// X^{-1} to Pinv_next; warps 4-7 skip the inversion.  smem: at least
+// 3 x 64 x GJP + 4 x 64 floats + one int, 16-byte aligned.
+template <typename T>
+__device__ __forceinline__ void pivot_next_wide(const T* A, int64_t n, int k, const T* Pinv, T* Pinv_next, int* info,
+                                                unsigned char* smem) {
+  float (*Ls)[GJP] = reinterpret_cast<float (*)[GJP]>(smem);
+  float (*Rc)[GJP] = Ls + GJB;
+  float (*L2s)[GJP] = Rc + GJB;
+  float (*prow)[GJB] = reinterpret_cast<float (*)[GJB]>(L2s + GJB);
+  float (*pcol)[GJB] = prow + 2;
+  int* bad = reinterpret_cast<int*>(pcol + 2);
+  const int k1 = k + 1;
+  const int kb = int((n - int64_t(k1) * GJB) < GJB ? (n - int64_t(k1) * GJB) : GJB);
+  const int64_t o = int64_t(k) * GJB, o1 = int64_t(k1) * GJB;
+  const int tid = threadIdx.x, bi = tid % 16, bj = tid / 16;
+  copy_cols_async<256>(Pinv, GJB, 0, 0, Ls);         // P^{-1}
+  copy_cols_async<256>(A, n, o, o1, Rc);             // A[k, k+1]
+  copy_cols_async<256>(A, n, o1, o, L2s);            // A[k+1, k]
+  cp_async_commit();
+  float x[4][4], t[4][4];
+  {
+    const int64_t r = o1 + 4 * bi;                   // A[k+1, k+1], this thread's 4 x 4
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t c = o1 + 4 * bj + v;
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < n && c < n) q = __ldcg(reinterpret_cast<const float4*>(A + r + n * c));   // L2: A may be new
+      x[0][v] = q.x;
+      x[1][v] = q.y;
+      x[2][v] = q.z;
+      x[3][v] = q.w;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[u][v] = 0.f;
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  tile_fma_cc4<1>(Ls, Rc, t);                        // t = P^{-1} A[k, k+1]
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < 4; ++v)                        // Rc <- t, by columns
+    *reinterpret_cast<float4*>(&Rc[4 * bj + v][4 * bi]) = make_float4(t[0][v], t[1][v], t[2][v], t[3][v]);
+  __syncthreads();
+  tile_fma_cc4<-1>(L2s, Rc, x);                      // x = A[k+1,k+1] - A[k+1,k] t
+#pragma unroll
+  for (int v = 0; v < 4; ++v)                        // X -> Ls, by columns (Ls was last read before t)
+    *reinterpret_cast<float4*>(&Ls[4 * bj + v][4 * bi]) = make_float4(x[0][v], x[1][v], x[2][v], x[3][v]);
+  __syncthreads();
+  if (tid < GJT) {
+    float y[4][8];                                   // the 4 x 8 layout of gj_invert_tile
+    const int ci = tid % 16, cj = tid / 16;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const float4 q = *reinterpret_cast<const float4*>(&Ls[8 * cj + v][4 * ci]);
+      y[0][v] = q.x;
+      y[1][v] = q.y;
+      y[2][v] = q.z;
+      y[3][v] = q.w;
+    }
+    pad_identity(y, kb);
+    pivot_store<true>(y, n, k1, kb, Pinv_next, nullptr, info, prow, pcol, bad);
+  }
+}
+
+// One sweep of the tensor-core path in one launch (n % 4 == 0, k0 = 64 k).
+// CTA 0 forms and inverts the pivot of sweep k + 1 from this sweep's input
+// (pivot_next_wide).
+// CTA 1 + ib + mt jb produces the output tile of rows i0 = 128 ib .. + 127
+// and columns j0 = 128 jb .. + 127 in two rounds of tensor-core products:
+//   (1) its slice of the row panel, transposed: for l < 64 and j in the tile,
+//           Rt[j, l] = sum_m A[k0 + m, j] P^{-1}[l, m]
+//       with A[k, k] taken as the identity, so that the columns of block k
+//       get P^{-1} itself (M = 128 rows j, N = 64, K = 64, TMEM columns
+//       128 .. 191); the CTAs whose rows hold block k store it as rows k of
+//       B (B[k, j] = P^{-1} A[k, j], B[k, k] = P^{-1});
+//   (2) the rank-64 update of the tile from Rt (TMEM columns 0 .. 127):
+//           B[i, j] = A[i, j] - sum_l A[i, k0 + l] Rt[j, l]   (j outside block k)
+//           B[i, j] = -sum_l A[i, k0 + l] Rt[j, l]             (j in block k)
+//       stored for the rows i outside block k.
+// Every float32 operand enters as three bfloat16 pieces and six piece
+// products (float32-level products, float32 accumulation in TMEM).  This
+// replaces the separate row-panel launch and the side-stream pivot launch of
+// a sweep by one launch.
+constexpr int kSwPPiece = GJB * GJB * 2;                             // one piece of P^{-1}: 8 KB
+constexpr int kSwPc = 3 * kUtPiece;                                  // column-panel pieces (rows i)
+constexpr int kSwRt = 3 * kUtPiece;                                  // A[k, J]^T pieces, then Rt pieces (rows j)
+constexpr int kSwPp = 3 * kSwPPiece;                                 // P^{-1} pieces (rows l)
+constexpr int kSwStageOff = kSwPc + kSwRt + kSwPp;                   // 120 KB
+constexpr int kSwStage = (GJB * kUtM + kUtN * GJP + GJB * GJP) * 4;  // sa, sk, sp: 83 KB >= 128 x 128 x 4
+constexpr int kSwSmem = kSwStageOff + kSwStage;                      // 203 KB
+static_assert(kSwStage >= kUtM * kUtN * 4, "the output tile is staged where the operands were");
+static_assert(kSwSmem + 1024 <= 227 * 1024, "one CTA per SM");
+
+// Output tile t = ib + mt jb of sweep k (256 threads): operands, the two
+// rounds of products and the stores.  bar: an initialised mbarrier whose next
+// two phases have parities 0 and 1; tb: 256 allocated TMEM columns.  Returns
+// false when a wait for the products ran out (the tile is then not written,
+// *info = n + 1, the timeout counter grows, and the products last committed
+// have been waited for once more, bounded).
+template <typename T>
+__device__ bool sweep_tile(const T* A, T* B, const T* Pk, int64_t n, int k, int t, unsigned char* sw_smem,
+                           uint64_t* barp, uint32_t tb, int* info, int* tmo) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* apc = sw_smem;                                      // A[I, k] pieces, rows i
+  unsigned char* rpc = sw_smem + kSwPc;                              // A[k, J]^T pieces, then Rt pieces, rows j
+  unsigned char* ppc = sw_smem + kSwPc + kSwRt;                      // P^{-1} pieces, rows l
+  float (*sa)[kUtM] = reinterpret_cast<float (*)[kUtM]>(sw_smem + kSwStageOff);   // [l][i]
+  float (*sk)[GJP] = reinterpret_cast<float (*)[GJP]>(sw_smem + kSwStageOff + GJB * kUtM * 4);  // [j][m]
+  float (*sp)[GJP] = sk + kUtN;                                      // [m][l]
+  float (*si)[kUtM] = sa;                                            // [j][i], the output tile, at the end
+  uint64_t& bar = *barp;
+  const int mt = int((n + kUtM - 1) / kUtM);
+  const int64_t i0 = int64_t(t % mt) * kUtM, j0 = int64_t(t / mt) * kUtN, k0 = int64_t(k) * GJB;
+  // the operands of (1) first (A[k0 + m, j0 + j], not for j in block k, and
+  // P^{-1}), then the column panel A[i0 + r, k0 + l], split while (1) runs
+#pragma unroll
+  for (int q = 0; q < kUtN * GJB / 4 / 256; ++q) {
+    const int e = tid + 256 * q, j = e / 16, m = 4 * (e % 16);
+    const int64_t jj = j0 + j;
+    if (jj / GJB == k) continue;
+    const bool in = jj < n && k0 + m < n;
+    cp_async16(&sk[j][m], in ? A + (k0 + m) + n * jj : A, in);
+  }
+#pragma unroll
+  for (int q = 0; q < GJB * GJB / 4 / 256; ++q) {
+    const int e = tid + 256 * q, m = e / 16, l = 4 * (e % 16);
+    cp_async16(&sp[m][l], Pk + l + GJB * m, true);
+  }
+  cp_async_commit();
+#pragma unroll
+  for (int q = 0; q < GJB * kUtM / 4 / 256; ++q) {
+    const int e = tid + 256 * q, l = e / 32, r = 4 * (e % 32);
+    const bool in = i0 + r < n && k0 + l < n;
+    cp_async16(&sa[l][r], in ? A + (i0 + r) + n * (k0 + l) : A, in);
+  }
+  cp_async_commit();
+  cp_async_wait<1>();
+  __syncthreads();
+  const int row = tid & 127, l0 = 32 * (tid >> 7);
+  float v[32];
+  {
+    const int64_t jj = j0 + row;
+    if (jj / GJB == k) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) v[c] = (int64_t(l0 + c) == jj - k0) ? 1.f : 0.f;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; c += 4) {
+        const float4 x4 = *reinterpret_cast<const float4*>(&sk[row][l0 + c]);
+        v[c] = x4.x;
+        v[c + 1] = x4.y;
+        v[c + 2] = x4.z;
+        v[c + 3] = x4.w;
+      }
+    }
+    ut_store_half(rpc, row, l0, v);
+    if (tid < 128) {
+      const int pr = tid & 63, p0 = 32 * (tid >> 6);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) v[c] = sp[p0 + c][pr];
+      ut_store_half<kSwPPiece>(ppc, pr, p0, v);
+    }
+  }
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  constexpr int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+  if (tid == 0) {                                 // (1) Rt in TMEM columns 128 .. 191
+    const uint32_t id = tc::idesc_bf16(kUtN, GJB, false, false);
+    const uint32_t sr_ = tc::smem_u32(rpc), sp_ = tc::smem_u32(ppc);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int ks = 0; ks < GJB / 16; ++ks)
+        tc::mma_bf16(tb + 128, tc::sdesc(sr_ + pa[c] * kUtPiece + ks * 256, 128, 1024),
+                     tc::sdesc(sp_ + pb[c] * kSwPPiece + ks * 256, 128, 1024), id, (c | ks) ? 1u : 0u);
+    tc::mma_commit(&bar);
+  }
+  __syncwarp();
+  cp_async_wait<0>();
+  __syncthreads();                                // the column panel has landed
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = sa[l0 + c][row];
+  ut_store_half(apc, row, l0, v);
+  int ph = 0;                                     // commits made so far - 1
+  // after this barrier no thread reads the staging area any more
+  bool ok = __syncthreads_and(tc::mbar_wait(&bar, 0u) ? 1 : 0) != 0;
+  // the tile of A to subtract from, while the rest runs
+#pragma unroll
+  for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {
+    const int e = tid + 256 * q, c = e / 32, r = 4 * (e % 32);
+    const bool in = i0 + r < n && j0 + c < n;
+    cp_async16(&si[c][r], in ? A + (i0 + r) + n * (j0 + c) : A, in);
+  }
+  cp_async_commit();
+  if (ok) {
+    tc::tc_fence_after();
+    // warp w: rows j = 32 (w % 4) + lane, l = 32 (w / 4) .. + 31
+    const int qr = warp & 3, lw = 32 * (warp >> 2), j = 32 * qr + lane;
+    tc::tmem_ld32(tb + (uint32_t(32 * qr) << 16) + 128u + uint32_t(lw), v);
+    const int64_t jj = j0 + j;
+    if (k0 >= i0 && k0 < i0 + kUtM && jj < n) {   // rows k of B
+#pragma unroll
+      for (int c = 0; c < 32; c += 4)
+        if (k0 + lw + c < n)
+          *reinterpret_cast<float4*>(B + (k0 + lw + c) + n * jj) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+    }
+    ut_store_half(rpc, j, lw, v);                 // the products of (1) have read rpc
+    tc::fence_async_smem();                       // (and the column-panel pieces written above)
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (tid == 0) {                               // (2) the update in TMEM columns 0 .. 127
+      const uint32_t id = tc::idesc_bf16(kUtM, kUtN, false, false);
+      const uint32_t sa_ = tc::smem_u32(apc), sr_ = tc::smem_u32(rpc);
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int ks = 0; ks < GJB / 16; ++ks)
+          tc::mma_bf16(tb, tc::sdesc(sa_ + pa[c] * kUtPiece + ks * 256, 128, 1024),
+                       tc::sdesc(sr_ + pb[c] * kUtPiece + ks * 256, 128, 1024), id, (c | ks) ? 1u : 0u);
+      tc::mma_commit(&bar);
+    }
+    __syncwarp();
+    ph = 1;
+    cp_async_wait<0>();
+    ok = __syncthreads_and(tc::mbar_wait(&bar, 1u) ? 1 : 0) != 0;
+  }
+  cp_async_wait<0>();
+  if (ok) {
+    // warp w: TMEM lanes (rows) 32 (w % 4) .., columns 64 (w / 4) .. + 63;
+    // the result replaces the staged tile (lanes = rows: no bank is read
+    // twice), then the CTA stores it along the columns, 16 bytes a thread
+    // (storing each warp's 32 rows of a column from registers took 6.9K
+    // cycles against 4.8K)
+    tc::tc_fence_after();
+    const int qr = warp & 3, cbase = 64 * (warp >> 2), r = 32 * qr + lane;
+#pragma unroll 1
+    for (int c0 = cbase; c0 < cbase + 64; c0 += 32) {
+      float d[32];
+      tc::tmem_ld32(tb + (uint32_t(32 * qr) << 16) + uint32_t(c0), d);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int64_t j = j0 + c0 + c;
+        si[c0 + c][r] = ((j / GJB == k) ? 0.f : si[c0 + c][r]) - d[c];
+      }
+    }
+  }
+  __syncthreads();
+  if (ok) {
+#pragma unroll 4
+    for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {   // four rows per copy: a 64-row block never splits one
+      const int e = tid + 256 * q, c = e / 32, rr = 4 * (e % 32);
+      const int64_t i = i0 + rr, j = j0 + c;
+      if (i < n && j < n && i / GJB != k)
+        *reinterpret_cast<float4*>(B + i + n * j) = *reinterpret_cast<const float4*>(&si[c][rr]);
+    }
+  } else {
+    if (tid == 0) {
+      if (tmo) atomicAdd(tmo, 1);
+      if (info) atomicCAS(info, 0, int(n + 1));
+    }
+    tc::mbar_wait(&bar, uint32_t(ph) & 1u);       // bounded drain of the products last committed
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  return ok;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_sweep_tc(const T* A, T* B, const T* Pk, T* Pn, int64_t n, int k,
+                                                     const int* skip, int* info, int* tmo) {
+  pdl_enter();
+  if (skip && *skip) return;
+  extern __shared__ __align__(1024) unsigned char sw_smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tbase_s;
+  const int nt = int((n + GJB - 1) / GJB);
+  if (blockIdx.x == 0) {                          // the pivot of sweep k + 1
+    if (k + 1 < nt) pivot_next_wide<T>(A, n, k, Pk, Pn, info, sw_smem);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(&tbase_s, 256);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tb = tbase_s;
+  sweep_tile<T>(A, B, Pk, n, k, int(blockIdx.x) - 1, sw_smem, &bar, tb, info, tmo);
+  if (threadIdx.x < 32) tc::tmem_dealloc(tb, 256);
 }
 
 // Invert the n x n SPD matrix A (full storage, column-major); B is the second
@@ -926,18 +1271,35 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, c
 // the first ident / GJB sweeps are replaced by one block elimination.  With
 // side != null the pivot of sweep k + 1 is inverted on `side` while sweep k's
 // row panel and update run on s (fork/join through ev_fork / ev_join,
-// graph-capturable).
+// graph-capturable).  The tensor-core path (n % 4 == 0, n >= kUtMinN or
+// tc_mode == 1) runs a sweep as one k_gj_sweep_tc launch while its 1 + mt^2
+// CTAs fit on the GPU at once.  (All sweeps in one launch, separated by grid
+// barriers on global sync words, measured slower: 253 against 240 us at
+// n = 1200 from the first sweep.)
 template <typename T>
 int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const int* skip, cudaStream_t s,
               cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, T** result, int tc_mode) {
   // the rank-64 updates on the tensor cores from n = kUtMinN (tc_mode < 0),
   // or as tc_mode says (0: SIMT, 1: tensor cores)
   const bool use_tc = n % 4 == 0 && (tc_mode < 0 ? (n >= kUtMinN) : (tc_mode != 0));
+  // one launch per sweep (k_gj_sweep_tc) while its 1 + mt^2 CTAs fit on the
+  // GPU at once; beyond that each of its CTAs recomputing its slice of the
+  // row panel costs more than a row-panel launch (n = 2700: 1.30 against
+  // 1.16 ms), and the sweep runs as row panel + k_gj_update_tc with the
+  // pivot on the side stream
+  const unsigned mt = unsigned((n + kUtM - 1) / kUtM);
+  int nsm = 0, dev = 0;
+  if (use_tc && (cudaGetDevice(&dev) != cudaSuccess ||
+                 cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+    return CP_ECUDA;
+  const bool fused = use_tc && 1 + int64_t(mt) * mt <= nsm;
   int* tmo = nullptr;
   if (use_tc) {
     if (tc_timeout_counter(&tmo) != CP_OK) return CP_ECUDA;
     if (cudaFuncSetAttribute(k_gj_update_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUtSmemAll) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_gj_sweep_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSwSmem) !=
+            cudaSuccess)
       return CP_ECUDA;
   }
   if (side && (cudaFuncSetAttribute(k_gj_pivot_next<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -980,7 +1342,12 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
   for (int k = k0; k < nt; ++k) {
     T* pk = pinv + size_t(k & 1) * GJB * GJB;
     T* pn = pinv + size_t((k + 1) & 1) * GJB * GJB;
-    if (nt > 1) {
+    if (nt > 1 && fused) {
+      // one launch per sweep: the next pivot in CTA 0, the row panel and the update in the others
+      if (launch_pdl(k_gj_sweep_tc<T>, 1 + mt * mt, 256, kSwSmem, s, static_cast<const T*>(src), dst,
+                     static_cast<const T*>(pk), pn, n, k, skip, info, tmo) != cudaSuccess)
+        return CP_ECUDA;
+    } else if (nt > 1) {
       const bool next = (k + 1 < nt);
       if (next && side) {
         if (cudaEventRecord(ev_fork, s) != cudaSuccess) return CP_ECUDA;
@@ -990,15 +1357,11 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
         if (cudaEventRecord(ev_join, side) != cudaSuccess) return CP_ECUDA;
       }
       if (use_tc) {
-        const unsigned mt = unsigned((n + kUtM - 1) / kUtM), ntc = unsigned((n + kUtN - 1) / kUtN);
-        if (n % 4 == 0 ? launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk,
-                                    skip) != cudaSuccess
-                       : launch_pdl(k_gj_rowpanel<T, false>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk,
-                                    skip) != cudaSuccess)
-          return CP_ECUDA;
-        if (launch_pdl(k_gj_update_tc<T>, dim3(mt, ntc), 256, kUtSmemAll, s, static_cast<const T*>(src), dst,
-                       static_cast<const T*>(dst), n, int64_t(0), int64_t(k) * GJB, 1, k, (next && side) ? 1 : 0, skip,
-                       info, tmo) != cudaSuccess)
+        if (launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk, skip) !=
+                cudaSuccess ||
+            launch_pdl(k_gj_update_tc<T>, dim3(mt, mt), 256, kUtSmemAll, s, static_cast<const T*>(src), dst,
+                       static_cast<const T*>(dst), n, int64_t(0), int64_t(k) * GJB, 1, k, (next && side) ? 1 : 0,
+                       skip, info, tmo) != cudaSuccess)
           return CP_ECUDA;
       } else if (n % 4 == 0) {
         if (launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk, skip) !=

@@ -84,17 +84,6 @@ __device__ __forceinline__ uint32_t coff(int row, int col, int gs) {
   return uint32_t((row >> 3) * gs + (col >> 3) * 128 + (row & 7) * 16 + (col & 7) * 2);
 }
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& x0, __nv_bfloat16& x1, __nv_bfloat16& x2) {
-  x0 = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(x0);
-  x1 = __float2bfloat16_rn(r1);
-  x2 = __float2bfloat16_rn(r1 - __bfloat162float(x1));
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return uint32_t(__bfloat16_as_ushort(lo)) | (uint32_t(__bfloat16_as_ushort(hi)) << 16);
-}
-
 // Pieces of row `row` of the A1 chunk (i1 = row index in A1): the R factor
 // values are all loaded first, rounded once to float32 and split into three
 // bfloat16 pieces in float32 arithmetic.  A float64 split would run its
@@ -110,12 +99,7 @@ __device__ __forceinline__ void build_a1_row(const double* a, int64_t I1, int R,
     uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      __nv_bfloat16 x0[2], x1[2], x2[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) split3(v[rg * 8 + h * 2 + q], x0[q], x1[q], x2[q]);
-      w0[h] = pack2(x0[0], x0[1]);
-      w1[h] = pack2(x1[0], x1[1]);
-      w2[h] = pack2(x2[0], x2[1]);
+      tc::split3x2(v[rg * 8 + h * 2], v[rg * 8 + h * 2 + 1], w0[h], w1[h], w2[h]);
     }
     *reinterpret_cast<uint4*>(apc + coff(row, rg * 8, kArow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
     *reinterpret_cast<uint4*>(apc + coff(row, 32 + rg * 8, kArow)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
@@ -162,15 +146,8 @@ __device__ __forceinline__ void build_w(unsigned char* wbuf, const float (&a2)[3
     uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      __nv_bfloat16 x0[2], x1[2], x2[2];
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int r = rg * 8 + h * 2 + e;
-        split3(a2[r] * a3[r], x0[e], x1[e], x2[e]);
-      }
-      w0[h] = pack2(x0[0], x0[1]);
-      w1[h] = pack2(x1[0], x1[1]);
-      w2[h] = pack2(x2[0], x2[1]);
+      const int r = rg * 8 + h * 2;
+      tc::split3x2(a2[r] * a3[r], a2[r + 1] * a3[r + 1], w0[h], w1[h], w2[h]);
     }
     *reinterpret_cast<uint4*>(wbuf + coff(tid, rg * 8, kWrow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
     *reinterpret_cast<uint4*>(wbuf + coff(tid, 32 + rg * 8, kWrow)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
@@ -193,12 +170,7 @@ __device__ __forceinline__ void build_a1_half(const double* a, int64_t I1, int R
     uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      __nv_bfloat16 x0[2], x1[2], x2[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) split3(v[rh * 8 + h * 2 + q], x0[q], x1[q], x2[q]);
-      w0[h] = pack2(x0[0], x0[1]);
-      w1[h] = pack2(x1[0], x1[1]);
-      w2[h] = pack2(x2[0], x2[1]);
+      tc::split3x2(v[rh * 8 + h * 2], v[rh * 8 + h * 2 + 1], w0[h], w1[h], w2[h]);
     }
     const int c = 16 * g + rh * 8;
     *reinterpret_cast<uint4*>(apc + coff(row, c, kArow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
@@ -214,15 +186,8 @@ __device__ __forceinline__ void build_w_half(unsigned char* wbuf, const float (&
     uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      __nv_bfloat16 x0[2], x1[2], x2[2];
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int j = rh * 8 + h * 2 + e;
-        split3(a2[j] * a3[16 * g + j], x0[e], x1[e], x2[e]);
-      }
-      w0[h] = pack2(x0[0], x0[1]);
-      w1[h] = pack2(x1[0], x1[1]);
-      w2[h] = pack2(x2[0], x2[1]);
+      const int j = rh * 8 + h * 2;
+      tc::split3x2(a2[j] * a3[16 * g + j], a2[j + 1] * a3[16 * g + j + 1], w0[h], w1[h], w2[h]);
     }
     const int c = 16 * g + rh * 8;
     *reinterpret_cast<uint4*>(wbuf + coff(row, c, kWrow)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);

@@ -205,5 +205,21 @@ __device__ __forceinline__ void tma_prefetch_3d(const void* tmap, int x, int y, 
                : "memory");
 }
 
+// Three bfloat16 pieces of two float32 values a (low half) and b (high half),
+// each pair packed in one 32-bit word: x = x0 + x1 + x2 with every piece
+// rounded to nearest (24 significant bits in all, exact for normal x).  One
+// packed conversion per piece pair; bfloat16 -> float32 is a shift.
+__device__ __forceinline__ void split3x2(float a, float b, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+  uint32_t p;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(b), "f"(a));
+  w0 = p;
+  const float ra = a - __uint_as_float(p << 16), rb = b - __uint_as_float(p & 0xFFFF0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(rb), "f"(ra));
+  w1 = p;
+  const float sa = ra - __uint_as_float(p << 16), sb = rb - __uint_as_float(p & 0xFFFF0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(sb), "f"(sa));
+  w2 = p;
+}
+
 }  // namespace tc
 }  // namespace cpdgn
