@@ -40,10 +40,15 @@ def general_spd(n, seed):
     return (B @ B.T / n + 0.05 * np.eye(n)).astype(np.float32)
 
 
-# large cores (the 400^3, R = 30 core is n = 2700) and n % 4 != 0 (scalar operand loads)
+# large cores (the 400^3, R = 30 core is n = 2700) and n % 4 != 0 (scalar operand loads).
+# From n = 1024 (n % 4 == 0) a sweep is one launch of 1 + ceil(n / 128)^2 CTAs
+# while they fit on the GPU (n <= 1536: 1024, 1100 with a 12-row last pivot
+# block, 1200, 1536 with 145 CTAs), else the row-panel launch + update
+# (1600: 170 CTAs, 2700).
 @pytest.mark.parametrize("n,block,ident", [(1200, 400, 400), (900, 225, 225), (75, 25, 25), (130, 0, 0),
                                            (64, 0, 0), (50, 0, 0), (257, 0, 0), (2700, 900, 900),
-                                           (1600, 0, 0), (1537, 0, 0)])
+                                           (1600, 0, 0), (1537, 0, 0), (1024, 256, 256), (1100, 0, 0),
+                                           (1536, 0, 0)])
 def test_inverse_matches_float64(cp, n, block, ident):
     M = spd_with_identity_blocks(n, block, 7 + n) if block else general_spd(n, 7 + n)
     ref = np.linalg.inv(M.astype(np.float64))
@@ -62,6 +67,18 @@ def test_not_spd_sets_info(cp):
     n = 96
     M = general_spd(n, 3)
     M[70, 70] = -5.0                    # a negative diagonal entry: a pivot must fail
+    A = torch.from_numpy(np.asfortranarray(M).ravel(order="F").copy()).cuda()
+    _, info = cp.SpdInverse(n, 0).run(A)
+    torch.cuda.synchronize()
+    assert int(info.item()) > 0
+
+
+@pytest.mark.parametrize("n,bad", [(1100, 1050), (1200, 700)])
+def test_not_spd_sets_info_one_launch_sweeps(cp, n, bad):
+    """A failing pivot inside the one-launch sweeps (the pivot of the last,
+    ragged block at n = 1100; a middle block at n = 1200) sets info."""
+    M = general_spd(n, 5)
+    M[bad, bad] = -5.0
     A = torch.from_numpy(np.asfortranarray(M).ravel(order="F").copy()).cuda()
     _, info = cp.SpdInverse(n, 0).run(A)
     torch.cuda.synchronize()
