@@ -926,16 +926,16 @@ __global__ void __launch_bounds__(GJT) k_gj_pivot_next(T* A, int64_t n, int k, c
   pivot_next_body<T, ASYNC>(A, n, k, Pinv, Pinv_next, info, Ls, Rc, L2s, prow, pcol, &bad, A);
 }
 
-// x += SGN L R on a 64 x 64 tile with 256 threads: thread (bi, bj) =
-// (tid % 16, tid / 16) owns rows 4 bi .. + 3 and columns 4 bj .. + 3; L and
-// R stored by columns (Lc[l][r] = L(r, l), Rc[c][l] = R(l, c)).  Four inner
-// steps per iteration: four float4 of L and four of R for 64 multiply-adds.
+// x += SGN L R over the inner indices l0 .. l0 + 31 only, thread (bi, bj)
+// owning rows 4 bi .. + 3 and columns 8 bj .. + 7 (the layout of
+// tile_fma_cc, for one 128-thread group of a larger CTA); L and R stored by
+// columns.
 template <int SGN>
-__device__ __forceinline__ void tile_fma_cc4(const float (*Lc)[GJP], const float (*Rc)[GJP], float (&x)[4][4]) {
-  const int bi = threadIdx.x % 16, bj = threadIdx.x / 16;
-#pragma unroll 4
-  for (int l = 0; l < GJB; l += 4) {
-    float a[4][4], b[4][4];
+__device__ __forceinline__ void tile_fma_cc_k32(const float (*Lc)[GJP], const float (*Rc)[GJP], float (&x)[4][8],
+                                                int bi, int bj, int l0) {
+#pragma unroll 2
+  for (int l = l0; l < l0 + 32; l += 4) {
+    float a[4][4], b[8][4];
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const float4 t = *reinterpret_cast<const float4*>(&Lc[l + w][4 * bi]);
@@ -945,8 +945,8 @@ __device__ __forceinline__ void tile_fma_cc4(const float (*Lc)[GJP], const float
       a[w][3] = SGN * t.w;
     }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const float4 t = *reinterpret_cast<const float4*>(&Rc[4 * bj + v][l]);
+    for (int v = 0; v < 8; ++v) {
+      const float4 t = *reinterpret_cast<const float4*>(&Rc[8 * bj + v][l]);
       b[v][0] = t.x;
       b[v][1] = t.y;
       b[v][2] = t.z;
@@ -957,76 +957,75 @@ __device__ __forceinline__ void tile_fma_cc4(const float (*Lc)[GJP], const float
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) x[u][v] = fmaf(a[w][u], b[v][w], x[u][v]);
+        for (int v = 0; v < 8; ++v) x[u][v] = fmaf(a[w][u], b[v][w], x[u][v]);
+  }
+}
+
+// Partial tile of group 1 into T (by columns) / added from T by group 0.
+__device__ __forceinline__ void tile_put_cols(const float (&x)[4][8], float (*T)[GJP], int bi, int bj) {
+#pragma unroll
+  for (int v = 0; v < 8; ++v)
+    *reinterpret_cast<float4*>(&T[8 * bj + v][4 * bi]) = make_float4(x[0][v], x[1][v], x[2][v], x[3][v]);
+}
+__device__ __forceinline__ void tile_add_cols(float (&x)[4][8], const float (*T)[GJP], int bi, int bj) {
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const float4 q = *reinterpret_cast<const float4*>(&T[8 * bj + v][4 * bi]);
+    x[0][v] += q.x;
+    x[1][v] += q.y;
+    x[2][v] += q.z;
+    x[3][v] += q.w;
   }
 }
 
 // The pivot of sweep k + 1 as pivot_next_body forms it (n % 4 == 0), inside
-// a 256-thread CTA: the two products on all eight warps (two warps per
-// scheduler hide the shared-memory latency that bounds the products of the
-// 128-thread form: about 3.6K and 4.0K cycles there), then X passes through
-// shared memory to warps 0-3, which invert it (named barrier 1) and write
-// X^{-1} to Pinv_next; warps 4-7 skip the inversion.  smem: at least
-// 3 x 64 x GJP + 4 x 64 floats + one int, 16-byte aligned.
+// a 256-thread CTA.  Each product is split over the inner index: warps 0-3
+// take l < 32 and warps 4-7 l >= 32, both in the 4 x 8 layout of the
+// inversion, and the second half is added through shared memory (two
+// warps per scheduler; the 128-thread products took 3.6K and 4.0K cycles,
+// 256 threads on 4 x 4 entries over the whole inner index 4.0K and 3.8K).
+// Warps 0-3 then hold X in their registers, invert it (named barrier 1) and
+// write X^{-1} to Pinv_next.  smem: at least 4 x 64 x GJP + 4 x 64 floats +
+// one int, 16-byte aligned.
 template <typename T>
 __device__ __forceinline__ void pivot_next_wide(const T* A, int64_t n, int k, const T* Pinv, T* Pinv_next, int* info,
                                                 unsigned char* smem) {
   float (*Ls)[GJP] = reinterpret_cast<float (*)[GJP]>(smem);
   float (*Rc)[GJP] = Ls + GJB;
   float (*L2s)[GJP] = Rc + GJB;
-  float (*prow)[GJB] = reinterpret_cast<float (*)[GJB]>(L2s + GJB);
+  float (*Ts)[GJP] = L2s + GJB;
+  float (*prow)[GJB] = reinterpret_cast<float (*)[GJB]>(Ts + GJB);
   float (*pcol)[GJB] = prow + 2;
   int* bad = reinterpret_cast<int*>(pcol + 2);
   const int k1 = k + 1;
   const int kb = int((n - int64_t(k1) * GJB) < GJB ? (n - int64_t(k1) * GJB) : GJB);
   const int64_t o = int64_t(k) * GJB, o1 = int64_t(k1) * GJB;
-  const int tid = threadIdx.x, bi = tid % 16, bj = tid / 16;
+  const int tid = threadIdx.x, grp = tid >> 7, bi = tid % 16, bj = (tid & 127) / 16;
   copy_cols_async<256>(Pinv, GJB, 0, 0, Ls);         // P^{-1}
   copy_cols_async<256>(A, n, o, o1, Rc);             // A[k, k+1]
   copy_cols_async<256>(A, n, o1, o, L2s);            // A[k+1, k]
   cp_async_commit();
-  float x[4][4], t[4][4];
-  {
-    const int64_t r = o1 + 4 * bi;                   // A[k+1, k+1], this thread's 4 x 4
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int64_t c = o1 + 4 * bj + v;
-      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < n && c < n) q = __ldcg(reinterpret_cast<const float4*>(A + r + n * c));   // L2: A may be new
-      x[0][v] = q.x;
-      x[1][v] = q.y;
-      x[2][v] = q.z;
-      x[3][v] = q.w;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) t[u][v] = 0.f;
-    }
-  }
+  float x[4][8], t[4][8];
+  if (grp == 0) load_block(A, n, o1, o1, x);         // A[k+1, k+1]
+  else zero_block(x);
+  zero_block(t);
   cp_async_wait<0>();
   __syncthreads();
-  tile_fma_cc4<1>(Ls, Rc, t);                        // t = P^{-1} A[k, k+1]
+  tile_fma_cc_k32<1>(Ls, Rc, t, bi, bj, 32 * grp);   // t = P^{-1} A[k, k+1], half the inner index
+  if (grp == 1) tile_put_cols(t, Ts, bi, bj);
   __syncthreads();
-#pragma unroll
-  for (int v = 0; v < 4; ++v)                        // Rc <- t, by columns
-    *reinterpret_cast<float4*>(&Rc[4 * bj + v][4 * bi]) = make_float4(t[0][v], t[1][v], t[2][v], t[3][v]);
+  if (grp == 0) {
+    tile_add_cols(t, Ts, bi, bj);
+    tile_put_cols(t, Rc, bi, bj);                    // Rc <- t, by columns
+  }
   __syncthreads();
-  tile_fma_cc4<-1>(L2s, Rc, x);                      // x = A[k+1,k+1] - A[k+1,k] t
-#pragma unroll
-  for (int v = 0; v < 4; ++v)                        // X -> Ls, by columns (Ls was last read before t)
-    *reinterpret_cast<float4*>(&Ls[4 * bj + v][4 * bi]) = make_float4(x[0][v], x[1][v], x[2][v], x[3][v]);
+  tile_fma_cc_k32<-1>(L2s, Rc, x, bi, bj, 32 * grp); // x = A[k+1,k+1] - A[k+1,k] t, half the inner index
+  if (grp == 1) tile_put_cols(x, Ts, bi, bj);
   __syncthreads();
-  if (tid < GJT) {
-    float y[4][8];                                   // the 4 x 8 layout of gj_invert_tile
-    const int ci = tid % 16, cj = tid / 16;
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      const float4 q = *reinterpret_cast<const float4*>(&Ls[8 * cj + v][4 * ci]);
-      y[0][v] = q.x;
-      y[1][v] = q.y;
-      y[2][v] = q.z;
-      y[3][v] = q.w;
-    }
-    pad_identity(y, kb);
-    pivot_store<true>(y, n, k1, kb, Pinv_next, nullptr, info, prow, pcol, bad);
+  if (grp == 0) {
+    tile_add_cols(x, Ts, bi, bj);
+    pad_identity(x, kb);
+    pivot_store<true>(x, n, k1, kb, Pinv_next, nullptr, info, prow, pcol, bad);
   }
 }
 
