@@ -861,10 +861,11 @@ __device__ __forceinline__ void tile_fma_cc(const float (*Lc)[GJP], const float 
 // of one column) per copy, zero outside n x n.  Needs n % 4 == 0 (then every
 // source address is 16-byte aligned: r0 and r are multiples of 4).  NT threads.
 template <int NT>
-__device__ __forceinline__ void copy_cols_async(const float* A, int64_t n, int64_t r0, int64_t c0, float (*S)[GJP]) {
+__device__ __forceinline__ void copy_cols_async(const float* A, int64_t n, int64_t r0, int64_t c0, float (*S)[GJP],
+                                                int t = int(threadIdx.x)) {
 #pragma unroll
   for (int q = 0; q < GJB * GJB / 4 / NT; ++q) {
-    const int e = int(threadIdx.x) + q * NT;
+    const int e = t + q * NT;
     const int r = 4 * (e % 16), c = e / 16;
     const int64_t gr = r0 + r, gc = c0 + c;
     const bool in = gr < n && gc < n;
@@ -1264,6 +1265,54 @@ __global__ void __launch_bounds__(256) k_gj_sweep_tc(const T* A, T* B, const T* 
   if (threadIdx.x < 32) tc::tmem_dealloc(tb, 256);
 }
 
+// The first pivot after the one-launch elimination of the leading identity
+// block (k0 panels), formed from the matrix before that elimination:
+//     X = A[k0, k0] - sum_{c < k0} A[k0, c] A[c, k0]
+// (the identity block's own pivot is I), inverted, X^{-1} into Pinv.  It
+// depends on the input alone, so it runs on the side stream while the
+// identity elimination runs (n % 4 == 0).  256 threads: group g (warps
+// 4g .. 4g + 3) sums the blocks c = g, g + 2, ... in the 4 x 8 layout of the
+// inversion, each group with its own operand buffers and named barrier
+// (2 + g); group 1's sum is added through shared memory and group 0 inverts.
+constexpr int kPivIdentSmem = (5 * GJB * GJP + 4 * GJB) * 4 + 16;
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_pivot_ident(const T* A, int64_t n, int k0, T* Pinv, int* info,
+                                                        const int* skip) {
+  pdl_enter();
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char pi_smem[];
+  float (*Ts)[GJP] = reinterpret_cast<float (*)[GJP]>(pi_smem);
+  const int tid = threadIdx.x, grp = tid >> 7, lt = tid & 127, bi = lt % 16, bj = lt / 16;
+  float (*Lc)[GJP] = Ts + GJB * (1 + 2 * grp);       // A[k0, c], by columns
+  float (*Rc)[GJP] = Lc + GJB;                       // A[c, k0], by columns
+  float (*prow)[GJB] = reinterpret_cast<float (*)[GJB]>(Ts + 5 * GJB);
+  float (*pcol)[GJB] = prow + 2;
+  int* bad = reinterpret_cast<int*>(pcol + 2);
+  const int kb = int((n - int64_t(k0) * GJB) < GJB ? (n - int64_t(k0) * GJB) : GJB);
+  const int64_t o = int64_t(k0) * GJB;
+  float x[4][8];
+  if (grp == 0) load_block(A, n, o, o, x);
+  else zero_block(x);
+  for (int c = grp; c < k0; c += 2) {
+    const int64_t oc = int64_t(c) * GJB;
+    copy_cols_async<128>(A, n, o, oc, Lc, lt);
+    copy_cols_async<128>(A, n, oc, o, Rc, lt);
+    cp_async_commit();
+    cp_async_wait<0>();
+    asm volatile("bar.sync %0, 128;\n" ::"r"(2 + grp) : "memory");
+    tile_fma_cc_k32<-1>(Lc, Rc, x, bi, bj, 0);
+    tile_fma_cc_k32<-1>(Lc, Rc, x, bi, bj, 32);
+    asm volatile("bar.sync %0, 128;\n" ::"r"(2 + grp) : "memory");   // buffers free for the next block
+  }
+  if (grp == 1) tile_put_cols(x, Ts, bi, bj);
+  __syncthreads();
+  if (grp == 0) {
+    tile_add_cols(x, Ts, bi, bj);
+    pad_identity(x, kb);
+    pivot_store<true>(x, n, k0, kb, Pinv, nullptr, info, prow, pcol, bad);
+  }
+}
+
 // Invert the n x n SPD matrix A (full storage, column-major); B is the second
 // buffer and pinv holds 2 GJB x GJB blocks.  *result receives the buffer with
 // the inverse.  When the leading `ident` rows/columns of A are the identity,
@@ -1311,11 +1360,23 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
   T* dst = B;
   int k0 = int(ident / GJB);
   if (k0 >= nt) k0 = nt - 1;
+  // with one-launch sweeps the first pivot is formed from the input on the
+  // side stream while the identity block is eliminated
+  const bool pivot0_side = fused && side && k0 > 0;
   if (k0 > 0) {
     if (n % 4 == 0) {
       if (cudaFuncSetAttribute(k_gj_identity<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kIdentSmem) != cudaSuccess)
         return CP_ECUDA;
+      if (pivot0_side) {
+        if (cudaFuncSetAttribute(k_gj_pivot_ident<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kPivIdentSmem) != cudaSuccess ||
+            cudaEventRecord(ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess)
+          return CP_ECUDA;
+        k_gj_pivot_ident<T><<<1, 256, kPivIdentSmem, side>>>(src, n, k0, pinv + size_t(k0 & 1) * GJB * GJB, info,
+                                                             skip);
+        if (cudaEventRecord(ev_join, side) != cudaSuccess) return CP_ECUDA;
+      }
       if (launch_pdl(k_gj_identity<T, true>, nt * nt * 2, GJTH, kIdentSmem, s, src, dst, n, k0, use_tc ? 1 : 0,
                      skip) != cudaSuccess)
         return CP_ECUDA;
@@ -1335,9 +1396,12 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
     src = dst;
     dst = t;
   }
-  if (launch_pdl(k_gj_pivot<T>, 1, GJT, 0, s, src, dst, n, k0, pinv + size_t(k0 & 1) * GJB * GJB, info, skip) !=
-      cudaSuccess)
+  if (pivot0_side) {
+    if (cudaStreamWaitEvent(s, ev_join, 0) != cudaSuccess) return CP_ECUDA;
+  } else if (launch_pdl(k_gj_pivot<T>, 1, GJT, 0, s, src, dst, n, k0, pinv + size_t(k0 & 1) * GJB * GJB, info,
+                        skip) != cudaSuccess) {
     return CP_ECUDA;
+  }
   for (int k = k0; k < nt; ++k) {
     T* pk = pinv + size_t(k & 1) * GJB * GJB;
     T* pn = pinv + size_t((k + 1) & 1) * GJB * GJB;
