@@ -58,7 +58,7 @@ TRAFFIC_TC_200 = 32.286208e6           # k_mttkrp_tc, 200^3 R=20, float32 tensor
 TRAFFIC_TC_512 = 539.364e6             # k_mttkrp_tc, 512^3 R=32, float32 tensor (mean of two launches)
 # summed over the kernels of one float32 core inverse (n = 1200), every kernel
 # with cold caches under ncu (bytes)
-GJ_TRAFFIC = 84.255e6
+GJ_TRAFFIC = 84.523e6
 # timed runs restart from their initial factors every this many launches
 RESTART_EVERY = 50
 
