@@ -52,10 +52,10 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per launch, dram__bytes_read.sum + dram__bytes_write.sum from
 # one ncu capture of the kernel (bytes); None where the kernel has changed
 # since its counters were taken.
-TRAFFIC_TC3_200 = 32.299520e6          # k_mttkrp_tc3, 200^3 R=20, two-plane tensor
-TRAFFIC_TC3_512 = 537.898752e6 + 2.792192e6   # k_mttkrp_tc3, 512^3 R=32
-TRAFFIC_TC_200 = 32.286208e6           # k_mttkrp_tc, 200^3 R=20, float32 tensor
-TRAFFIC_TC_512 = 539.364e6             # k_mttkrp_tc, 512^3 R=32, float32 tensor (mean of two launches)
+TRAFFIC_TC3_200 = 32.2932e6             # k_mttkrp_tc3, 200^3 R=20, two-plane tensor (mean of two launches)
+TRAFFIC_TC3_512 = 539.4846e6            # k_mttkrp_tc3, 512^3 R=32 (mean of two launches)
+TRAFFIC_TC_200 = 32.2857e6              # k_mttkrp_tc, 200^3 R=20, float32 tensor (mean of two launches)
+TRAFFIC_TC_512 = 539.4094e6             # k_mttkrp_tc, 512^3 R=32, float32 tensor (mean of two launches)
 # summed over the kernels of one float32 core inverse (n = 1200), every kernel
 # with cold caches under ncu (bytes)
 GJ_TRAFFIC = 84.523e6
