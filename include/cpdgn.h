@@ -247,11 +247,15 @@ int cp_dgn_solve(const cp_shape* shape, const double* a, const double* mu, doubl
  *   pinv   2 x 64 x 64 float32 of scratch.
  *   info   device int (may be NULL): receives 0, or the 1-based index of
  *          the first non-positive or non-finite pivot (the result is then
- *          not an inverse).
+ *          not an inverse), or n + 1 if a bounded wait of the tensor-core
+ *          kernels (n % 4 == 0, n >= 1024) ran out.
  *   in_work  host int: receives 1 if the inverse is left in work, 0 if in A
  *          (fixed by n and ident, known before the device work runs).
- * Enqueued on `stream`; the pivot chain runs on a second stream of the
- * library, forked from and joined back to `stream` (graph-capturable).
+ * Enqueued on `stream`.  From n = 1024 (n % 4 == 0) up to n = 1536 a sweep
+ * is one launch whose first CTA forms and inverts the next pivot block, and
+ * the first pivot after the identity block is formed on a second stream of
+ * the library; otherwise every next pivot is.  The second stream is forked
+ * from and joined back to `stream` (graph-capturable).
  * CP_EINVAL for null pointers, n < 1, ident < 0 or ident > n. */
 int cp_spd_invert_f32(int64_t n, int64_t ident, float* A, float* work, float* pinv, int* info,
                       int* in_work, void* stream);
