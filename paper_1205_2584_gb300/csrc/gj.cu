@@ -631,6 +631,124 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* A, T* B, const T*
   if (warp == 0) tc::tmem_dealloc(tb, 128);
 }
 
+// The rank-64 update of one sweep above the one-launch size (the row panel
+// already in B): B[i, j] = init - sum_l A[i, k0 + l] B[k0 + l, j] with init
+// 0 in column block k, else A[i, j]; rows of block k and, with skip_pivot,
+// tile (k + 1, k + 1) are not written.  Same products as k_gj_update_tc,
+// but with only the bfloat16 pieces in shared memory (96 KB), so that two
+// CTAs share an SM and one's loads and split overlap the other's products
+// and stores: each thread splits its operand half-rows straight from global
+// memory (a warp's loads of the column panel are 128-byte rows), the tile of
+// A to subtract from is read per 32-column chunk into registers, and the
+// result is staged for the 16-byte stores where the pieces were.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_gj_update2_tc(const T* A, T* B, int64_t n, int k, int skip_pivot,
+                                                          const int* skip, int* info, int* tmo) {
+  pdl_enter();
+  if (skip && *skip) return;
+  extern __shared__ __align__(1024) unsigned char u2_smem[];
+  unsigned char* apc = u2_smem;                    // column-panel pieces, rows = i
+  unsigned char* rpc = u2_smem + 3 * kUtPiece;     // row-panel pieces, rows = j
+  float (*st)[kUtM] = reinterpret_cast<float (*)[kUtM]>(u2_smem);   // [j][i], the result, at the end
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tbase_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t i0 = int64_t(blockIdx.x) * kUtM, j0 = int64_t(blockIdx.y) * kUtN, k0 = int64_t(k) * GJB;
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase_s, 128);
+    tc::tmem_relinquish();
+  }
+  {
+    const int row = tid & 127, l0 = 32 * (tid >> 7);
+    float v[32];
+    const int64_t i = i0 + row;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = (i < n && k0 + l0 + c < n) ? A[i + n * (k0 + l0 + c)] : 0.f;
+    ut_store_half(apc, row, l0, v);
+    const int64_t j = j0 + row;
+#pragma unroll
+    for (int c = 0; c < 32; c += 4) {
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < n && k0 + l0 + c < n) q = *reinterpret_cast<const float4*>(B + (k0 + l0 + c) + n * j);
+      v[c] = q.x;
+      v[c + 1] = q.y;
+      v[c + 2] = q.z;
+      v[c + 3] = q.w;
+    }
+    ut_store_half(rpc, row, l0, v);
+  }
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tb = tbase_s;
+  if (tid == 0) {
+    const uint32_t id = tc::idesc_bf16(kUtM, kUtN, false, false);
+    const uint32_t sa_ = tc::smem_u32(apc), sr_ = tc::smem_u32(rpc);
+    constexpr int pa[6] = {0, 0, 1, 1, 0, 2}, pr[6] = {0, 1, 0, 1, 2, 0};
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int ks = 0; ks < GJB / 16; ++ks)
+        tc::mma_bf16(tb, tc::sdesc(sa_ + pa[c] * kUtPiece + ks * 256, 128, 1024),
+                     tc::sdesc(sr_ + pr[c] * kUtPiece + ks * 256, 128, 1024), id, (c | ks) ? 1u : 0u);
+    tc::mma_commit(&bar);
+  }
+  __syncwarp();
+  // warp w: TMEM lanes (rows) 32 (w % 4) .., columns 64 (w / 4) .. + 63
+  const int qr = warp & 3, cbase = 64 * (warp >> 2), r = 32 * qr + lane;
+  const int64_t i = i0 + r;
+  float cv[32];                                    // the first chunk of A's tile, while the products run
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const int64_t j = j0 + cbase + c;
+    cv[c] = (i < n && j < n && j / GJB != k) ? A[i + n * j] : 0.f;
+  }
+  const bool ok = __syncthreads_and(tc::mbar_wait(&bar, 0u) ? 1 : 0) != 0;
+  if (ok) {
+    tc::tc_fence_after();
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int c0 = cbase + 32 * h;
+      if (h == 1) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int64_t j = j0 + c0 + c;
+          cv[c] = (i < n && j < n && j / GJB != k) ? A[i + n * j] : 0.f;
+        }
+      }
+      float d[32];
+      tc::tmem_ld32(tb + (uint32_t(32 * qr) << 16) + uint32_t(c0), d);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) st[c0 + c][r] = cv[c] - d[c];   // the pieces are dead: the products are done
+    }
+  }
+  __syncthreads();
+  if (ok) {
+#pragma unroll 4
+    for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {   // four rows per copy: a 64-row block never splits one
+      const int e = tid + 256 * q, c = e / 32, rr = 4 * (e % 32);
+      const int64_t ii = i0 + rr, j = j0 + c;
+      const int64_t bi = ii / GJB, bj = j / GJB;
+      if (ii < n && j < n && bi != k && !(skip_pivot && bi == k + 1 && bj == k + 1))
+        *reinterpret_cast<float4*>(B + ii + n * j) = *reinterpret_cast<const float4*>(&st[c][rr]);
+    }
+  } else {
+    if (tid == 0) {
+      if (tmo) atomicAdd(tmo, 1);
+      if (info) atomicCAS(info, 0, int(n + 1));
+    }
+    tc::mbar_wait(&bar, 0u);                       // bounded drain of the products
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tb, 128);
+}
+
 // The first kb0 tiles of the core lie inside its leading identity block
 // (the core's diagonal R^2 x R^2 blocks are I).  Eliminating them at once
 // (pivot I of size kb0 * GJB) maps A -> B as
@@ -1347,6 +1465,8 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
     if (cudaFuncSetAttribute(k_gj_update_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUtSmemAll) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_gj_sweep_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSwSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_gj_update2_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUtSmem) !=
             cudaSuccess)
       return CP_ECUDA;
   }
@@ -1422,9 +1542,8 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
       if (use_tc) {
         if (launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk, skip) !=
                 cudaSuccess ||
-            launch_pdl(k_gj_update_tc<T>, dim3(mt, mt), 256, kUtSmemAll, s, static_cast<const T*>(src), dst,
-                       static_cast<const T*>(dst), n, int64_t(0), int64_t(k) * GJB, 1, k, (next && side) ? 1 : 0,
-                       skip, info, tmo) != cudaSuccess)
+            launch_pdl(k_gj_update2_tc<T>, dim3(mt, mt), 256, kUtSmem, s, static_cast<const T*>(src), dst, n, k,
+                       (next && side) ? 1 : 0, skip, info, tmo) != cudaSuccess)
           return CP_ECUDA;
       } else if (n % 4 == 0) {
         if (launch_pdl(k_gj_rowpanel<T, true>, (nt - 1) * 2, GJTH, kTileSmem, s, src, dst, n, k, pk, skip) !=
