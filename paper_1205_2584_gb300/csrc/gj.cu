@@ -13,10 +13,20 @@
 // (1-based row); nothing traps.
 //
 // The sequential part is the chain of pivot inverses.  P^{-1} of sweep k + 1
-// is formed and inverted during sweep k by one CTA (k_gj_pivot_next) on a side
-// stream, from sweep k's input alone, so it overlaps sweep k's row panel and
-// update.  That CTA reserves nearly all of its SM's shared memory, so no tile
-// CTA shares the SM with it.
+// is formed and inverted during sweep k from sweep k's input alone, so it
+// overlaps sweep k's row panel and update: by one CTA (k_gj_pivot_next) on a
+// side stream that reserves nearly all of its SM's shared memory (so no tile
+// CTA shares the SM with it), or, on the tensor-core path while the grid fits
+// on the GPU, by CTA 0 of the sweep's single launch (k_gj_sweep_tc), whose
+// other CTAs form their slices of the row panel themselves.  The kernels by
+// path (n = N R^2):
+//   n % 4 != 0 or n < 1024: k_gj_identity, k_gj_pivot, then per sweep
+//     k_gj_pivot_next (side stream), k_gj_rowpanel, k_gj_update;
+//   1024 <= n, 1 + ceil(n / 128)^2 CTAs fit: k_gj_identity + k_gj_update_tc
+//     (identity block) with k_gj_pivot_ident (side stream), then one
+//     k_gj_sweep_tc per sweep;
+//   larger n: k_gj_identity + k_gj_update_tc, k_gj_pivot, then per sweep
+//     k_gj_pivot_next (side stream), k_gj_rowpanel, k_gj_update2_tc.
 //
 // Tile products.  The pivot kernels (128 threads on a 64 x 64 tile): thread
 // (bi, bj) owns rows 4 bi .. 4 bi + 3 and columns 8 bj .. 8 bj + 7, so each
