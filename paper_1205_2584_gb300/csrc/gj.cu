@@ -433,18 +433,10 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
 
 // ---- rank-64 k updates on the tensor cores (tcgen05) ----
 //
-// One CTA (256 threads) per 128 x 128 output tile of a rank-(64 nkb) update
-//     B[i, j] = init(i, j) - sum_{l < 64 nkb} A[i, ko + l] R[ko + l, j],
-// in one of two modes:
-//   sweep k (k >= 0, nkb = 1, ko = 64 k, tiles over the whole matrix):
-//     R = row block k of B as the row panel left it (P^{-1} A[k, j], and
-//     P^{-1} itself in tile (k, k), where the pivot kernel stored it);
-//     init = 0 in column block k, else A[i, j]; rows of block k (the row
-//     panel's output) and, with skip_pivot, tile (k + 1, k + 1) (the
-//     next-pivot kernel's) are not written;
-//   identity elimination (k < 0, ko = 0, tiles over [base, n)^2 with
-//     base = 64 nkb): R = A, init = A[i, j] (the trailing part of the
-//     one-launch elimination of the leading identity block).
+// k_gj_update_tc: one CTA (256 threads) per 128 x 128 output tile of the
+// trailing part of the one-launch elimination of the leading identity block,
+// a rank-(64 nkb) update over the tiles of [base, n)^2 (base = 64 nkb):
+//     B[i, j] = A[i, j] - sum_{l < 64 nkb} A[i, l] A[l, j].
 // Per K block of 64 the two operand slices (128 x 64 of the column panel,
 // 64 x 128 of the row panel) are copied to a float32 staging area by
 // cp.async; each thread splits half a row of each into three bfloat16
@@ -456,6 +448,8 @@ __global__ void __launch_bounds__(GJTH) k_gj_update(const T* A, T* B, int64_t n,
 // copied.  Then the tile of A to subtract from is staged the same way, each
 // warp reads 32 lanes (rows) x 64 columns of the accumulator back into it,
 // and the CTA stores the result along the columns with 16-byte stores.
+// The sweeps use the same pieces and layout in k_gj_sweep_tc and
+// k_gj_update2_tc (below).
 // Every wait for the MMAs is bounded: when one runs out the tile is not
 // written, *info is set to n + 1 (the inverse is then rejected like one with
 // a bad pivot), the timeout counter grows, and the CTA waits once more
@@ -498,8 +492,8 @@ constexpr int kUtSmemAll = kUtSmem + kUtStage;
 // 16-byte copies of K block kb's operand slices into the staging area;
 // n % 4 == 0, so a copy is wholly inside or wholly outside the matrix
 template <typename T>
-__device__ __forceinline__ void ut_copy_slices(const T* A, const T* Rs, int64_t n, int64_t i0, int64_t j0,
-                                               int64_t kc, float (*sa)[kUtM], float (*sr)[GJP]) {
+__device__ __forceinline__ void ut_copy_slices(const T* A, int64_t n, int64_t i0, int64_t j0, int64_t kc,
+                                               float (*sa)[kUtM], float (*sr)[GJP]) {
   const int tid = threadIdx.x;
 #pragma unroll
   for (int q = 0; q < GJB * kUtM / 4 / 256; ++q) {           // A(i0 + r, kc + l)
@@ -508,18 +502,17 @@ __device__ __forceinline__ void ut_copy_slices(const T* A, const T* Rs, int64_t 
     cp_async16(&sa[l][r], in ? A + (i0 + r) + n * (kc + l) : A, in);
   }
 #pragma unroll
-  for (int q = 0; q < kUtN * GJB / 4 / 256; ++q) {           // R(kc + l, j0 + j)
+  for (int q = 0; q < kUtN * GJB / 4 / 256; ++q) {           // A(kc + l, j0 + j)
     const int e = tid + 256 * q, j = e / 16, l = 4 * (e % 16);
     const bool in = j0 + j < n && kc + l < n;
-    cp_async16(&sr[j][l], in ? Rs + (kc + l) + n * (j0 + j) : Rs, in);
+    cp_async16(&sr[j][l], in ? A + (kc + l) + n * (j0 + j) : A, in);
   }
   cp_async_commit();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gj_update_tc(const T* A, T* B, const T* Rs, int64_t n, int64_t base,
-                                                      int64_t ko, int nkb, int k, int skip_pivot, const int* skip,
-                                                      int* info, int* tmo) {
+__global__ void __launch_bounds__(256) k_gj_update_tc(const T* A, T* B, int64_t n, int64_t base, int nkb,
+                                                      const int* skip, int* info, int* tmo) {
   pdl_enter();
   if (skip && *skip) return;
   extern __shared__ __align__(1024) unsigned char ut_smem[];
@@ -540,7 +533,7 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* A, T* B, const T*
     tc::tmem_alloc(&tbase_s, 128);
     tc::tmem_relinquish();
   }
-  ut_copy_slices(A, Rs, n, i0, j0, ko, sa, sr);
+  ut_copy_slices(A, n, i0, j0, 0, sa, sr);
   const uint32_t id = tc::idesc_bf16(kUtM, kUtN, false, false);
   bool ok = true;
   int kb = 0;
@@ -586,7 +579,7 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* A, T* B, const T*
     }
     __syncwarp();
     if (kb + 1 < nkb) {
-      ut_copy_slices(A, Rs, n, i0, j0, ko + int64_t(kb + 1) * GJB, sa, sr);
+      ut_copy_slices(A, n, i0, j0, int64_t(kb + 1) * GJB, sa, sr);
     } else {                                       // the tile of A to subtract from, while the MMAs run
 #pragma unroll
       for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {
@@ -611,22 +604,16 @@ __global__ void __launch_bounds__(256) k_gj_update_tc(const T* A, T* B, const T*
       float d[32];
       tc::tmem_ld32(tb + (uint32_t(32 * qr) << 16) + uint32_t(c0), d);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int64_t j = j0 + c0 + c;
-        si[c0 + c][r] = ((k >= 0 && j / GJB == k) ? 0.f : si[c0 + c][r]) - d[c];
-      }
+      for (int c = 0; c < 32; ++c) si[c0 + c][r] -= d[c];
     }
   }
   __syncthreads();
   if (ok) {
-    // four rows per copy: a 64-row block boundary never splits one
 #pragma unroll 4
     for (int q = 0; q < kUtN * kUtM / 4 / 256; ++q) {
       const int e = tid + 256 * q, c = e / 32, rr = 4 * (e % 32);
       const int64_t i = i0 + rr, j = j0 + c;
-      const int64_t bi = i / GJB, bj = j / GJB;
-      if (i < n && j < n && !(k >= 0 && (bi == k || (skip_pivot && bi == k + 1 && bj == k + 1))))
-        *reinterpret_cast<float4*>(B + i + n * j) = *reinterpret_cast<const float4*>(&si[c][rr]);
+      if (i < n && j < n) *reinterpret_cast<float4*>(B + i + n * j) = *reinterpret_cast<const float4*>(&si[c][rr]);
     }
   } else {
     if (tid == 0) {
@@ -1513,8 +1500,8 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
       if (use_tc) {
         const int64_t base = int64_t(k0) * GJB;
         const unsigned t = unsigned((n - base + kUtM - 1) / kUtM);
-        if (launch_pdl(k_gj_update_tc<T>, dim3(t, t), 256, kUtSmemAll, s, static_cast<const T*>(src), dst,
-                       static_cast<const T*>(src), n, base, int64_t(0), k0, -1, 0, skip, info, tmo) != cudaSuccess)
+        if (launch_pdl(k_gj_update_tc<T>, dim3(t, t), 256, kUtSmemAll, s, static_cast<const T*>(src), dst, n, base,
+                       k0, skip, info, tmo) != cudaSuccess)
           return CP_ECUDA;
       }
     } else {
