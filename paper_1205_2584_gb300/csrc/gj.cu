@@ -1449,7 +1449,7 @@ int gj_invert(T* A, T* B, T* pinv, int64_t n, int64_t ident, int* info, const in
   // GPU at once; beyond that each of its CTAs recomputing its slice of the
   // row panel costs more than a row-panel launch (n = 2700, 485 CTAs: 1.16
   // against 1.11 ms per inverse), and the sweep runs as row panel +
-  // k_gj_update_tc with the pivot on the side stream
+  // k_gj_update2_tc with the pivot on the side stream
   const unsigned mt = unsigned((n + kUtM - 1) / kUtM);
   int nsm = 0, dev = 0;
   if (use_tc && (cudaGetDevice(&dev) != cudaSuccess ||
