@@ -75,8 +75,9 @@ def test_not_spd_sets_info(cp):
 
 @pytest.mark.parametrize("n,bad", [(1100, 1050), (1200, 700)])
 def test_not_spd_sets_info_one_launch_sweeps(cp, n, bad):
-    """A failing pivot inside the one-launch sweeps (the pivot of the last,
-    ragged block at n = 1100; a middle block at n = 1200) sets info."""
+    """A failing pivot inside the one-launch sweeps (in block 16 of 18 at
+    n = 1100, whose last block has 12 rows; in block 10 of 19 at n = 1200)
+    sets info."""
     M = general_spd(n, 5)
     M[bad, bad] = -5.0
     A = torch.from_numpy(np.asfortranarray(M).ravel(order="F").copy()).cuda()
